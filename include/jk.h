@@ -1,0 +1,203 @@
+/*
+ * jk.h -- C ABI of the Gamma-point periodic Coulomb (J) and exchange (K)
+ * matrix build over contracted Cartesian Gaussian shells with Ewald-split
+ * electron repulsion integrals (Wang, Hait, Unzueta, Zhang, Martinez,
+ * "Fast and Scalable GPU-Accelerated Quantum Chemistry for Periodic Systems
+ * with Gaussian Orbitals", arXiv:2410.22278).
+ *
+ * Units are atomic (bohr, hartree).  All entry points return a status code
+ * (JK_OK = 0, negative on failure) unless stated otherwise; no C++
+ * exception crosses this boundary.  jk_last_error() returns a thread-local
+ * description of the most recent failure on the calling thread.
+ *
+ * AO order: shells in input order; inside a shell the Cartesian components
+ * run lx descending, then ly descending (p: x y z; d: xx xy xz yy yz zz).
+ * Matrices are nbf x nbf, row-major, FP64, symmetric.
+ *
+ * Threads: a plan is immutable after creation except for its build
+ * workspace; jk_build calls on the same plan are serialised internally.
+ * Distinct plans may be built concurrently on distinct streams.
+ */
+#ifndef JK_H
+#define JK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define JK_OK 0
+#define JK_ERR_INVALID (-1)      /* bad argument: volume <= 0, exponent <= 0, nprim outside 1..16, NULL pointer */
+#define JK_ERR_UNSUPPORTED (-2)  /* angular momentum above 2 (d) */
+#define JK_ERR_OOM (-3)          /* device or host allocation failed, or the request exceeds a budget */
+#define JK_ERR_CUDA (-4)         /* a CUDA runtime or cuBLAS call failed */
+#define JK_ERR_TIMEOUT (-5)      /* a wait ran out of time (jk_wait, bounded device waits) */
+#define JK_ERR_DEVICE_CHECK (-6) /* a device-side bounds check tripped (an index outside its buffer) */
+#define JK_ERR_BUSY (-7)         /* no free slot / server shutting down */
+#define JK_ERR_NOT_FOUND (-8)    /* unknown ticket */
+
+/* ---- problem statement (Sections 2.1, 3.6) ------------------------------ */
+
+/* Lattice vectors as rows: lattice[0..2] = a, lattice[3..5] = b,
+ * lattice[6..8] = c (bohr).  |det| must be > 0. */
+typedef struct {
+    double lattice[9];
+} jk_cell;
+
+/* One contracted Cartesian shell (Eq. local_contracted_basis).  exps and
+ * coefs (raw contraction coefficients; normalised internally by Eq.
+ * local_normalization and to unit local self-overlap) are read during
+ * jk_plan_create only and may be freed afterwards.  center may lie in any
+ * lattice image. */
+typedef struct {
+    int l;              /* 0, 1, 2 (s, p, d); larger -> JK_ERR_UNSUPPORTED */
+    int nprim;          /* 1..16 */
+    const double *exps; /* nprim exponents > 0 (bohr^-2) */
+    const double *coefs;
+    double center[3];
+} jk_shell;
+
+/* The four lattice-sum thresholds of Section 3.6 (values <= 0 select the
+ * paper's default 1e-14) and the mixed-precision switch (Section 3.5):
+ * a shell quartet whose density-weighted Schwarz estimate is at or above
+ * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: automatic). */
+typedef struct {
+    double pair_R;   /* delta_pair-R, Eq. pbc_eri_pair_cutoff_implementation */
+    double pair_cs;  /* delta_pair-Cauchy-Schwarz, Eq. pbc_eri_cauchy_schwarz_cutoff_implementation */
+    double ewald_R;  /* delta_Ewald-R, Eq. pbc_eri_real_cutoff_implementation */
+    double ewald_K;  /* delta_Ewald-K, Eq. pbc_eri_reciprocal_cutoff_implementation */
+    double mixed_switch;
+} jk_cutoffs;
+
+typedef enum { JK_FP64 = 0, JK_MIXED = 1 } jk_precision;
+
+typedef struct jk_plan jk_plan; /* opaque; owns its device-resident pair and G data */
+
+/* Figures of a plan, filled by jk_plan_info. */
+typedef struct {
+    int nbf, nshell, n_classes;
+    int n_g;                       /* half-space reciprocal vectors kept */
+    long long n_shell_pairs;       /* unique shell pairs with at least one local pair */
+    long long n_pair_images;       /* unique shell-pair images (I, J, R) */
+    long long n_prim_pair_images;  /* local primitive pairs (Section 3.1) */
+    long long n_quartets;          /* unique shell-pair-image quartets evaluated in real space */
+    long long n_quartets_schwarz;  /* of those, with Schwarz product >= delta_pair-CS (the quartets/s unit) */
+    long long n_quartets_fp64;     /* quartets the mixed policy sends to FP64 (all of them under JK_FP64) */
+    long long n_r1_candidates;     /* lattice vectors scanned per primitive quartet */
+    double omega, g_max, r1_max, volume;
+    size_t device_bytes;           /* resident plan arrays */
+    size_t workspace_bytes;        /* per-build scratch owned by the plan */
+} jk_plan_stats;
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/* Build the plan for one cell (Sections 3.1, 3.3, 3.4): normalise the
+ * shells, build the local-pair lists over lattice images with the pair
+ * cut-offs of Eqs. 434 and 450 (minimum-image offsets, Eq.
+ * lattice_image_min_norm), Schwarz estimates (Eq. 445) and quartet classes,
+ * the reciprocal vector list, and upload everything to `device`.
+ * omega <= 0 selects Eq. omega_implementation with w = 10.
+ * cut == NULL means all defaults.  On success *out owns device memory until
+ * jk_plan_destroy.  Errors: JK_ERR_INVALID, JK_ERR_UNSUPPORTED, JK_ERR_OOM,
+ * JK_ERR_CUDA; *out is left NULL. */
+int jk_plan_create(const jk_cell *cell, const jk_shell *shells, int nshell, double omega, const jk_cutoffs *cut,
+                   jk_precision precision, int device, jk_plan **out);
+
+int jk_plan_info(const jk_plan *plan, jk_plan_stats *out);
+
+/* Host only (no device needed): the pair-list counts of Section 3.1 for a
+ * cell, as jk_plan_create would build them.  counts[0] ordered shell pairs
+ * with at least one local pair, counts[1] ordered primitive pairs kept,
+ * counts[2] ordered local primitive pairs (lattice images included),
+ * counts[3] unique shell-pair images, counts[4] half-space reciprocal
+ * vectors.  Same errors as jk_plan_create's argument checks. */
+int jk_pair_counts(const jk_cell *cell, const jk_shell *shells, int nshell, double omega, const jk_cutoffs *cut,
+                   long long counts[5]);
+
+/* Number of basis functions of the plan (or -1 for NULL). */
+int jk_plan_nbf(const jk_plan *plan);
+
+void jk_plan_destroy(jk_plan *plan);
+
+/* ---- build (Sections 2.5, 2.6, 3.2) --------------------------------------- */
+
+/* J_mn = sum_ls (mn|ls) D_ls and K_mn = sum_ls (ml|sn) D_ls at the Gamma
+ * point (Eqs. pbc_j_definition_k_sample and pbc_k_definition with k = 0),
+ * with (mn|ls) the Ewald-split periodic ERI of Eq. pbc_eri_general_final:
+ * the erfc real-space sum over R1, the reciprocal sum over K != 0 and the
+ * removed K = 0 background term.
+ * D, J, K: device pointers to nbf*nbf FP64, row-major, on the plan's
+ * device.  D must be symmetric; J and K are overwritten and come out
+ * symmetric; either may be NULL to skip it (K is the expensive one).
+ * Stream-ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default);
+ * returns after enqueueing.  Caller keeps ownership of D, J, K. */
+int jk_build(jk_plan *plan, const double *D, double *J, double *K, void *cuda_stream);
+
+/* Same as jk_build with HOST buffers (row-major FP64): copies D in, builds,
+ * copies J and K out, and synchronises the stream before returning. */
+int jk_build_host(jk_plan *plan, const double *D_host, double *J_host, double *K_host, void *cuda_stream);
+
+/* E_J = 1/2 sum_mn D_mn J_mn and E_K = -1/4 sum_mn D_mn K_mn (closed-shell
+ * density D = 2 C C^T; the paper gives only J and K).  D, J, K device
+ * pointers (J or K may be NULL, the energy is then 0).  Results are
+ * written to host scalars; synchronises `cuda_stream`. */
+int jk_energy(const jk_plan *plan, const double *D, const double *J, const double *K, double *e_coul, double *e_exch,
+              void *cuda_stream);
+
+/* Device time of each phase of the most recent jk_build on this plan, in
+ * milliseconds, from CUDA events recorded on the build's stream around the
+ * phase's kernels (waits for that build to finish).  ms[0] prologue (D
+ * scaling, zeroing), ms[1] real-space quartet kernels, ms[2] reciprocal
+ * structure factors, ms[3] reciprocal Coulomb contraction, ms[4]
+ * reciprocal exchange contraction, ms[5] background and assembly, ms[6]
+ * whole build; launches[0..6] the number of kernel launches per phase.
+ * n = number of slots the caller provides (<= 7 used). */
+int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
+
+/* Gamma overlap over the plan's pair list (Eq. pbc_overlap_formula),
+ * written to the device pointer S (nbf*nbf FP64); stream-ordered. */
+int jk_overlap(const jk_plan *plan, double *S, void *cuda_stream);
+
+/* Ewald energy of point charges (Eq. nuclear_repulsion_energy, including the
+ * removed K = 0 term -(4 pi/V)/(4 w^2) that a non-neutral set needs), on the
+ * host; q[n], xyz[3n] (bohr), delta = truncation of both sums (<= 0: 1e-14).
+ * A test instrument for the Ewald machinery. */
+int jk_ewald_point_charges(const jk_cell *cell, int n, const double *q, const double *xyz, double omega, double delta,
+                           double *energy);
+
+/* ---- serving: continuous batching of builds (host scheduler) ------------ */
+
+typedef struct jk_server jk_server;
+
+/* A request server on `device` that admits builds while the sum of the
+ * admitted plans' workspace stays within hbm_budget_bytes and at most
+ * max_slots builds are in flight; each slot owns a stream.  Errors:
+ * JK_ERR_INVALID, JK_ERR_CUDA, JK_ERR_OOM. */
+int jk_server_create(int device, size_t hbm_budget_bytes, int max_slots, jk_server **out);
+
+/* Queue one build of `plan` on device buffers D, J, K (as in jk_build);
+ * returns a ticket.  The plan and buffers must stay valid until jk_wait
+ * returns for that ticket.  JK_ERR_OOM if the plan alone exceeds the
+ * budget; JK_ERR_BUSY after shutdown began. */
+int jk_submit(jk_server *srv, jk_plan *plan, const double *D, double *J, double *K, long long *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a ticket.  On completion writes
+ * the build's status and its latency (submit to completion, seconds).
+ * JK_ERR_TIMEOUT if it has not finished; JK_ERR_NOT_FOUND for an unknown or
+ * already-collected ticket. */
+int jk_wait(jk_server *srv, long long ticket, int timeout_ms, int *build_status, double *latency_s);
+
+/* Drain in-flight work, then free the server (never frees caller buffers). */
+void jk_server_destroy(jk_server *srv);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+const char *jk_status_string(int status);
+const char *jk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JK_H */

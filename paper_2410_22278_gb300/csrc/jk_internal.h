@@ -1,0 +1,75 @@
+// Internal data layout shared by the host plan builder and the CUDA kernels.
+//
+// A plan holds, resident on the device:
+//   * shells: centre, angular momentum, primitive range, first AO index;
+//   * unique shell-pair images (I, J, R) -- the middle layer of the
+//     three-layer pair structure of Section 3.1 -- in canonical orientation
+//     (l_I >= l_J; for I == J only R >= 0 lexicographically), bucketed by
+//     angular class (l_I, l_J) and sorted by descending Schwarz estimate;
+//   * local primitive pairs (the bottom layer): P, P-A, P-B(R), p and the
+//     prefactor K = c_a c_b exp(-ab/p |A-B-R|^2) (Eq. E_recursion_0 folded
+//     into K), sorted by |K| inside each image;
+//   * the Boys-function Taylor table, the R1 candidate lattice vectors for
+//     the real-space sums and the half-space reciprocal vectors.
+#pragma once
+#include <stdint.h>
+
+#define JK_MAXL 2
+#define JK_MAXLQ (4 * JK_MAXL)   // highest total angular momentum of a quartet
+#define JK_NCLASS_MAX 6          // (la, lb) with la >= lb, la <= 2
+
+// Boys table: F_m(T_k) for T_k = k / JK_BOYS_INV_STEP, k = 0 .. JK_BOYS_NPTS-1,
+// m = 0 .. JK_BOYS_MCOL-1.  Above JK_BOYS_TMAX the asymptotic branch is used.
+#define JK_BOYS_INV_STEP 32
+#define JK_BOYS_TMAX 36.0
+#define JK_BOYS_NPTS (36 * 32 + 2)
+#define JK_BOYS_MCOL (JK_MAXLQ + 8)
+
+struct ShellRec {
+    double c[3];
+    int l, nprim, p0, ao;
+};
+
+struct SpiRec {      // one unique shell-pair image
+    int I, J;        // shells, canonical orientation
+    int pp0, npp;    // local primitive pairs [pp0, pp0 + npp)
+    int n[3];        // lattice image of J
+    float w;         // orbit weight: 0.5 for (I, I, R = 0), else 1
+    int spair;       // index of the unique shell pair (I, J)
+    double Q;        // Schwarz estimate (Eq. pbc_eri_cauchy_schwarz_cutoff_definition, summed over primitives)
+};
+
+struct PpiRec {      // one local primitive pair
+    double P[3];
+    double PA[3];    // P - A
+    double PB[3];    // P - (B + R)
+    double p;        // a + b
+    double K;        // c_a c_b exp(-ab/p |A - B - R|^2), normalised coefficients
+    double pad;
+};
+
+struct SpairRec {    // unique shell pair (I, J) with its images [spi0, spi0 + nspi)
+    int I, J, spi0, nspi;
+};
+
+struct PlanDev {
+    int nbf, nshell;
+    int nspi, nppi, nspair;
+    const ShellRec *shells;
+    const SpiRec *spi;
+    const PpiRec *ppi;
+    const SpairRec *spair;
+    const int *spi_order;        // spi indices grouped by shell pair (for the reciprocal build)
+    const double *boys;          // [JK_BOYS_NPTS][JK_BOYS_MCOL]
+    const float *boys_f;
+    const double *r1;            // [nr1][4]: x, y, z, |R|, sorted by |R|
+    int nr1;
+    const double *gvec;          // [ng][4]: Gx, Gy, Gz, sqrt(8 pi w(G) / V)
+    int ng;
+    const double *compf;         // Cartesian component factor of each AO
+    double L[9];                 // lattice rows a, b, c
+    double Finv[9];              // fractional coordinates f = Finv * r
+    double omega, inv_omega2;
+    double ewald_R;              // delta_Ewald-R
+    double volume;
+};

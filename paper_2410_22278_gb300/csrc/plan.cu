@@ -1,0 +1,636 @@
+// Host plan builder: everything of Sections 3.1, 3.3 and 3.4 of
+// arXiv:2410.22278 that happens once per geometry.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+
+#include "plan.h"
+
+namespace jk {
+
+static thread_local std::string g_last_error;
+int fail(int status, const std::string &msg)
+{
+    g_last_error = msg;
+    return status;
+}
+const char *last_error_str() { return g_last_error.c_str(); }
+
+static const double kPi = 3.14159265358979323846;
+
+static void inv3(const double *m, double *o)
+{
+    double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) + m[2] * (m[3] * m[7] - m[4] * m[6]);
+    o[0] = (m[4] * m[8] - m[5] * m[7]) / det;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+    o[3] = (m[5] * m[6] - m[3] * m[8]) / det;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+    o[6] = (m[3] * m[7] - m[4] * m[6]) / det;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
+// r = L^T n for lattice rows L
+static inline void lat_point(const double *L, double n0, double n1, double n2, double *r)
+{
+    for (int k = 0; k < 3; ++k) r[k] = n0 * L[k] + n1 * L[3 + k] + n2 * L[6 + k];
+}
+static inline void frac(const double *Finv, const double *r, double *f)
+{
+    for (int i = 0; i < 3; ++i) f[i] = Finv[3 * i] * r[0] + Finv[3 * i + 1] * r[1] + Finv[3 * i + 2] * r[2];
+}
+
+// Section 3.3: all lattice vectors R with |R - c| < r.  The bounding cube of
+// edge 2r about c is mapped to fractional indices; floor/ceil over its eight
+// corners bound a parallelepiped of lattice points, each then tested
+// against the sphere.
+template <class F>
+static void enumerate_sphere(const double *L, const double *Finv, const double *c, double r, F &&visit)
+{
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    for (int s = 0; s < 8; ++s) {
+        double corner[3] = {c[0] + ((s & 1) ? r : -r), c[1] + ((s & 2) ? r : -r), c[2] + ((s & 4) ? r : -r)}, f[3];
+        frac(Finv, corner, f);
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = std::min(lo[i], (int)std::floor(f[i]));
+            hi[i] = std::max(hi[i], (int)std::ceil(f[i]));
+        }
+    }
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int d = lo[2]; d <= hi[2]; ++d) {
+                double R[3];
+                lat_point(L, a, b, d, R);
+                double dx = R[0] - c[0], dy = R[1] - c[1], dz = R[2] - c[2];
+                if (dx * dx + dy * dy + dz * dz < r * r) visit(a, b, d, R);
+            }
+}
+
+// Eq. local_normalization (radial part) times the contraction coefficients,
+// rescaled to unit self-overlap of the local contracted function.
+static void normalise_shell(int l, int n, const double *a, const double *c, double *out)
+{
+    double s = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double x = 2.0 * std::sqrt(a[i] * a[j]) / (a[i] + a[j]);
+            s += c[i] * c[j] * std::pow(x, l + 1.5);
+        }
+    double inv = 1.0 / std::sqrt(s);
+    for (int i = 0; i < n; ++i) out[i] = c[i] * std::pow(2.0 * a[i] / kPi, 0.75) * std::pow(8.0 * a[i], 0.5 * l) * inv;
+}
+
+static double fact_ratio(int i)  // i!/(2i)!
+{
+    double r = 1;
+    for (int k = i + 1; k <= 2 * i; ++k) r /= k;
+    return r;
+}
+static double comp_factor(int lx, int ly, int lz) { return std::sqrt(fact_ratio(lx) * fact_ratio(ly) * fact_ratio(lz)); }
+static double comp_factor_max(int l) { return l == 0 ? 1.0 : (l == 1 ? std::sqrt(0.5) : 0.5); }
+
+// Smaller of the radii of Eqs. pbc_eri_pair_cutoff_implementation and
+// pbc_eri_cauchy_schwarz_cutoff_implementation; < 0 when either log is <= 0.
+static double pair_radius(double a, double b, double cc, double amin, double dR, double dCS)
+{
+    double p = a + b;
+    double x1 = std::sqrt(2.0) * std::pow(kPi, 1.25) * cc / (p * std::sqrt(p + 2.0 * amin) * dR);
+    double x2 = std::pow(2.0, 0.25) * std::pow(kPi, 1.25) * cc / (std::pow(p, 1.25) * dCS);
+    if (!(x1 > 1.0) || !(x2 > 1.0)) return -1.0;
+    return std::min(std::sqrt(p / (a * b) * std::log(x1)), std::sqrt(p / (a * b) * std::log(x2)));
+}
+
+static int pair_class(int la, int lb)  // la >= lb
+{
+    return la * (la + 1) / 2 + lb;
+}
+
+// F_m(T_k) table by the convergent series at the top order and downward
+// recursion, in long double.
+void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out)
+{
+    out.assign((size_t)ncol * npts, 0.0);
+    for (int k = 0; k < npts; ++k) {
+        long double T = (long double)k / (long double)inv_step;
+        long double e = expl(-T);
+        int M = ncol - 1;
+        long double term = 1.0L / (2 * M + 1), sum = term;
+        for (int j = 1; j < 100000; ++j) {
+            term *= 2.0L * T / (2 * M + 2 * j + 1);
+            sum += term;
+            if (term < 1e-24L * sum) break;
+        }
+        long double F = e * sum;
+        out[(size_t)k * ncol + M] = (double)F;
+        for (int m = M - 1; m >= 0; --m) {
+            F = (2.0L * T * F + e) / (2 * m + 1);
+            out[(size_t)k * ncol + m] = (double)F;
+        }
+    }
+}
+
+// Squared real-space radius for one primitive quartet: Eq.
+// pbc_eri_real_cutoff_implementation, widened for the Hermite polynomial
+// growth (2 alpha_w |X|)^L that the s-type derivation leaves out.  Returns
+// < 0 when the quartet has no term above delta.
+static double realspace_r2(double p, double q, double KK, double omega, double delta, int L)
+{
+    double alpha = p * q / (p + q);
+    double aw = 1.0 / (1.0 / p + 1.0 / q + 1.0 / (omega * omega));
+    double cw = std::sqrt(aw / alpha);
+    double C = 2.0 * std::pow(kPi, 2.5) / (p * q * std::sqrt(p + q)) * std::fabs(KK) * (1.0 - cw);
+    double lg = std::log(C / delta);
+    if (lg <= 0) return -1.0;
+    double r = std::sqrt(lg / aw);
+    for (int it = 0; it < 3; ++it) r = std::sqrt((lg + L * std::log(1.0 + 2.0 * aw * r)) / aw);
+    return r * r;
+}
+
+PlanDev Plan::dev() const
+{
+    PlanDev d{};
+    d.nbf = nbf;
+    d.nshell = nshell;
+    d.nspi = (int)spi.size();
+    d.nppi = (int)ppi.size();
+    d.nspair = (int)spair.size();
+    d.shells = d_shells;
+    d.spi = d_spi;
+    d.ppi = d_ppi;
+    d.spair = d_spair;
+    d.spi_order = d_spi_order;
+    d.boys = d_boys;
+    d.boys_f = d_boys_f;
+    d.r1 = d_r1;
+    d.nr1 = (int)(r1.size() / 4);
+    d.gvec = d_gvec;
+    d.ng = (int)(gvec.size() / 4);
+    d.compf = d_compf;
+    memcpy(d.L, L, sizeof L);
+    memcpy(d.Finv, Finv, sizeof Finv);
+    d.omega = omega;
+    d.inv_omega2 = 1.0 / (omega * omega);
+    d.ewald_R = cut.ewald_R;
+    d.volume = volume;
+    return d;
+}
+
+template <class T>
+static int upload(const std::vector<T> &h, T **d, size_t &bytes)
+{
+    size_t n = std::max<size_t>(h.size(), 1) * sizeof(T);
+    if (cudaMalloc((void **)d, n) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed for plan array");
+    if (!h.empty() && cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(JK_ERR_CUDA, "cudaMemcpy failed for plan array");
+    bytes += n;
+    return JK_OK;
+}
+
+static int alloc_ws(Plan *P)
+{
+    Workspace &w = P->ws;
+    size_t n2 = (size_t)P->nbf * P->nbf;
+    int ng = (int)(P->gvec.size() / 4);
+    // structure-factor chunk: M and Z, each 2*gc*n^2 doubles, kept within ~4 GB together
+    double budget = 4.0e9;
+    long long gc = (long long)(budget / (32.0 * (double)n2));
+    gc = std::max<long long>(1, std::min<long long>(gc, std::max(ng, 1)));
+    gc = std::min<long long>(gc, 4096);
+    w.gc = (int)gc;
+    size_t bytes = 0;
+    auto al = [&](double **ptr, size_t count) -> bool {
+        if (cudaMalloc((void **)ptr, std::max<size_t>(count, 1) * sizeof(double)) != cudaSuccess) return false;
+        bytes += std::max<size_t>(count, 1) * sizeof(double);
+        return true;
+    };
+    bool ok = al(&w.Dp, n2) && al(&w.X, n2) && al(&w.Y, n2) && al(&w.JLR, n2) && al(&w.KLR, n2) && al(&w.T1, n2) &&
+              al(&w.T2, n2) && al(&w.M, 2 * (size_t)gc * n2) && al(&w.Z, 2 * (size_t)gc * n2) && al(&w.rho, 2 * (size_t)gc) &&
+              al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16);
+    if (!ok) return fail(JK_ERR_OOM, "cudaMalloc failed for build workspace");
+    if (cudaMalloc((void **)&w.err, sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
+    cudaMemset(w.err, 0, sizeof(unsigned));
+    w.bytes = bytes + sizeof(unsigned);
+    return JK_OK;
+}
+
+int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double omega, const jk_cutoffs *cut,
+               jk_precision precision, int device, Plan **out)
+{
+    if (!out) return fail(JK_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!cell || !shells || nshell <= 0) return fail(JK_ERR_INVALID, "cell or shells missing");
+    if (precision != JK_FP64 && precision != JK_MIXED) return fail(JK_ERR_INVALID, "unknown precision");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(cell->lattice[i])) return fail(JK_ERR_INVALID, "lattice not finite");
+    for (int s = 0; s < nshell; ++s) {
+        const jk_shell &sh = shells[s];
+        if (sh.l < 0) return fail(JK_ERR_INVALID, "negative angular momentum");
+        if (sh.l > JK_MAXL) return fail(JK_ERR_UNSUPPORTED, "angular momentum above d");
+        if (sh.nprim < 1 || sh.nprim > 16) return fail(JK_ERR_INVALID, "nprim outside 1..16");
+        if (!sh.exps || !sh.coefs) return fail(JK_ERR_INVALID, "shell arrays missing");
+        for (int k = 0; k < sh.nprim; ++k)
+            if (!(sh.exps[k] > 0) || !std::isfinite(sh.exps[k]) || !std::isfinite(sh.coefs[k]))
+                return fail(JK_ERR_INVALID, "exponent <= 0 or non-finite coefficient");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(sh.center[k])) return fail(JK_ERR_INVALID, "centre not finite");
+    }
+    Plan *P = new Plan();
+    P->device = device;
+    P->precision = precision;
+    memcpy(P->L, cell->lattice, sizeof P->L);
+    {
+        double LT[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) LT[3 * i + j] = P->L[3 * j + i];
+        double det = P->L[0] * (P->L[4] * P->L[8] - P->L[5] * P->L[7]) - P->L[1] * (P->L[3] * P->L[8] - P->L[5] * P->L[6]) +
+                     P->L[2] * (P->L[3] * P->L[7] - P->L[4] * P->L[6]);
+        P->volume = std::fabs(det);
+        if (!(P->volume > 1e-8)) {
+            delete P;
+            return fail(JK_ERR_INVALID, "cell volume <= 0");
+        }
+        inv3(LT, P->Finv);
+    }
+    const double V = P->volume;
+    // Eq. omega_implementation with w = 10 when the caller leaves omega to us
+    P->omega = omega > 0 ? omega : std::pow(10.0 * kPi * kPi * kPi / (V * V), 1.0 / 6.0);
+    jk_cutoffs c{};
+    if (cut) c = *cut;
+    if (!(c.pair_R > 0)) c.pair_R = 1e-14;
+    if (!(c.pair_cs > 0)) c.pair_cs = 1e-14;
+    if (!(c.ewald_R > 0)) c.ewald_R = 1e-14;
+    if (!(c.ewald_K > 0)) c.ewald_K = 1e-14;
+    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-9;
+    P->cut = c;
+
+    // ---- shells, normalised coefficients, component factors
+    P->nshell = nshell;
+    std::vector<double> cn, ex;
+    int ao = 0, p0 = 0;
+    for (int s = 0; s < nshell; ++s) {
+        const jk_shell &sh = shells[s];
+        ShellRec r{};
+        for (int k = 0; k < 3; ++k) r.c[k] = sh.center[k];
+        r.l = sh.l;
+        r.nprim = sh.nprim;
+        r.p0 = p0;
+        r.ao = ao;
+        P->shells.push_back(r);
+        std::vector<double> tmp(sh.nprim);
+        normalise_shell(sh.l, sh.nprim, sh.exps, sh.coefs, tmp.data());
+        for (int k = 0; k < sh.nprim; ++k) {
+            cn.push_back(tmp[k]);
+            ex.push_back(sh.exps[k]);
+        }
+        for (int lx = sh.l; lx >= 0; --lx)
+            for (int ly = sh.l - lx; ly >= 0; --ly) P->compf.push_back(comp_factor(lx, ly, sh.l - lx - ly));
+        ao += (sh.l + 1) * (sh.l + 2) / 2;
+        p0 += sh.nprim;
+    }
+    P->nbf = ao;
+    const double amin = *std::min_element(ex.begin(), ex.end());
+
+    // ---- unique shell pairs I <= J, their primitive pairs and images
+    struct Img {
+        int n[3];
+        std::vector<std::pair<int, int>> pp;  // (prim of I, prim of J)
+    };
+    std::vector<SpiRec> spis;
+    std::vector<std::vector<PpiRec>> spi_ppis;
+    const double *L = P->L;
+    for (int I = 0; I < nshell; ++I) {
+        const ShellRec &sI = P->shells[I];
+        for (int J = I; J < nshell; ++J) {
+            const ShellRec &sJ = P->shells[J];
+            double d[3] = {sI.c[0] - sJ.c[0], sI.c[1] - sJ.c[1], sI.c[2] - sJ.c[2]}, f[3], s[3];
+            frac(P->Finv, d, f);
+            double nr[3] = {std::round(f[0]), std::round(f[1]), std::round(f[2])};
+            lat_point(L, nr[0], nr[1], nr[2], s);
+            double dmin[3] = {d[0] - s[0], d[1] - s[1], d[2] - s[2]};  // Eq. lattice_image_min_norm
+            std::map<std::array<int, 3>, std::vector<std::pair<int, int>>> imgs;
+            double fac = comp_factor_max(sI.l) * comp_factor_max(sJ.l);
+            for (int ia = 0; ia < sI.nprim; ++ia)
+                for (int ib = 0; ib < sJ.nprim; ++ib) {
+                    double a = ex[sI.p0 + ia], b = ex[sJ.p0 + ib];
+                    double r = pair_radius(a, b, std::fabs(cn[sI.p0 + ia] * cn[sJ.p0 + ib]) * fac, amin, c.pair_R, c.pair_cs);
+                    if (r <= 0) continue;
+                    enumerate_sphere(L, P->Finv, dmin, r, [&](int n0, int n1, int n2, const double *) {
+                        std::array<int, 3> key = {n0 + (int)nr[0], n1 + (int)nr[1], n2 + (int)nr[2]};
+                        imgs[key].push_back({ia, ib});
+                    });
+                }
+            if (imgs.empty()) continue;
+            P->n_shell_pairs++;
+            {  // ordered counts: (J, I, -R) mirrors (I, J, R) for I != J; for I == J both signs are enumerated
+                std::set<std::pair<int, int>> distinct;
+                long long nloc = 0;
+                for (auto &kv : imgs) {
+                    nloc += (long long)kv.second.size();
+                    for (auto &pr : kv.second) distinct.insert(pr);
+                }
+                const int m = I == J ? 1 : 2;
+                P->n_ord_shell_pairs += m;
+                P->n_ord_prim_pairs += m * (long long)distinct.size();
+                P->n_ord_local_pairs += m * nloc;
+            }
+            // canonical orientation: first shell has the larger l
+            bool swap = sI.l < sJ.l;
+            int F = swap ? J : I, S = swap ? I : J;
+            for (auto &kv : imgs) {
+                std::array<int, 3> n = kv.first;
+                if (swap) n = {-n[0], -n[1], -n[2]};
+                if (I == J) {  // keep R >= 0 lexicographically
+                    bool pos = n[0] > 0 || (n[0] == 0 && (n[1] > 0 || (n[1] == 0 && n[2] >= 0)));
+                    if (!pos) continue;
+                }
+                const ShellRec &sF = P->shells[F], &sS = P->shells[S];
+                double R[3];
+                lat_point(L, n[0], n[1], n[2], R);
+                double A[3] = {sF.c[0], sF.c[1], sF.c[2]}, B[3] = {sS.c[0] + R[0], sS.c[1] + R[1], sS.c[2] + R[2]};
+                double AB2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+                std::vector<PpiRec> pv;
+                double Q = 0;
+                for (auto &pr : kv.second) {
+                    int pa = swap ? pr.second : pr.first, pb = swap ? pr.first : pr.second;
+                    double a = ex[sF.p0 + pa], b = ex[sS.p0 + pb], p = a + b;
+                    PpiRec x{};
+                    for (int k = 0; k < 3; ++k) {
+                        x.P[k] = (a * A[k] + b * B[k]) / p;
+                        x.PA[k] = x.P[k] - A[k];
+                        x.PB[k] = x.P[k] - B[k];
+                    }
+                    x.p = p;
+                    x.K = cn[sF.p0 + pa] * cn[sS.p0 + pb] * std::exp(-a * b / p * AB2);
+                    pv.push_back(x);
+                    Q += std::pow(2.0, 0.25) * std::fabs(x.K) * std::pow(kPi / p, 1.25);  // Eq. 445 per primitive
+                }
+                std::sort(pv.begin(), pv.end(), [](const PpiRec &u, const PpiRec &v) { return std::fabs(u.K) > std::fabs(v.K); });
+                SpiRec sr{};
+                sr.I = F;
+                sr.J = S;
+                sr.npp = (int)pv.size();
+                sr.n[0] = n[0];
+                sr.n[1] = n[1];
+                sr.n[2] = n[2];
+                sr.w = (I == J && n[0] == 0 && n[1] == 0 && n[2] == 0) ? 0.5f : 1.0f;
+                sr.Q = Q;
+                spis.push_back(sr);
+                spi_ppis.push_back(std::move(pv));
+            }
+        }
+    }
+    // ---- sort images by class, then descending Schwarz estimate (Section 3.1)
+    std::vector<int> order(spis.size());
+    std::iota(order.begin(), order.end(), 0);
+    auto cls_of = [&](const SpiRec &s) { return pair_class(P->shells[s.I].l, P->shells[s.J].l); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        int ca = cls_of(spis[a]), cb = cls_of(spis[b]);
+        if (ca != cb) return ca < cb;
+        return spis[a].Q > spis[b].Q;
+    });
+    for (int idx : order) {
+        SpiRec s = spis[idx];
+        s.pp0 = (int)P->ppi.size();
+        for (auto &x : spi_ppis[idx]) P->ppi.push_back(x);
+        P->spi.push_back(s);
+    }
+    for (int cl = 0; cl < JK_NCLASS_MAX; ++cl) {
+        ClassRange cr{};
+        cr.la = cl == 0 ? 0 : (cl <= 2 ? 1 : 2);
+        cr.lb = cl - cr.la * (cr.la + 1) / 2;
+        cr.b0 = (int)P->spi.size();
+        cr.b1 = 0;
+        for (int i = 0; i < (int)P->spi.size(); ++i)
+            if (cls_of(P->spi[i]) == cl) {
+                cr.b0 = std::min(cr.b0, i);
+                cr.b1 = std::max(cr.b1, i + 1);
+            }
+        if (cr.b1 <= cr.b0) cr.b0 = cr.b1 = 0;
+        P->classes.push_back(cr);
+    }
+    // ---- unique shell pairs with their images (reciprocal-space build), grouped by class
+    {
+        std::map<std::pair<int, int>, std::vector<int>> byp;
+        for (int i = 0; i < (int)P->spi.size(); ++i) byp[{P->spi[i].I, P->spi[i].J}].push_back(i);
+        std::vector<std::pair<int, int>> keys;
+        for (auto &kv : byp) keys.push_back(kv.first);
+        std::stable_sort(keys.begin(), keys.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+            return pair_class(P->shells[a.first].l, P->shells[a.second].l) < pair_class(P->shells[b.first].l, P->shells[b.second].l);
+        });
+        P->spair_class_off.assign(JK_NCLASS_MAX + 1, 0);
+        for (auto &k : keys) {
+            SpairRec r{};
+            r.I = k.first;
+            r.J = k.second;
+            r.spi0 = (int)P->spi_order.size();
+            for (int i : byp[k]) {
+                P->spi[i].spair = (int)P->spair.size();
+                P->spi_order.push_back(i);
+            }
+            r.nspi = (int)P->spi_order.size() - r.spi0;
+            P->spair_class_off[pair_class(P->shells[r.I].l, P->shells[r.J].l) + 1]++;
+            P->spair.push_back(r);
+        }
+        for (int i = 0; i < JK_NCLASS_MAX; ++i) P->spair_class_off[i + 1] += P->spair_class_off[i];
+    }
+    // ---- quartet counts (unique pairs of images), Schwarz-significant ones
+    {
+        long long N = (long long)P->spi.size();
+        P->n_quartets = N * (N + 1) / 2;
+        std::vector<double> q(N);
+        for (long long i = 0; i < N; ++i) q[i] = P->spi[i].Q;
+        std::sort(q.begin(), q.end(), std::greater<double>());
+        long long cnt = 0, cnt64 = 0;
+        long long j = N - 1, j64 = N - 1;
+        for (long long i = 0; i < N; ++i) {
+            while (j >= i && q[i] * q[j] < c.pair_cs) --j;
+            if (j >= i) cnt += j - i + 1;
+            while (j64 >= i && q[i] * q[j64] < P->mixed_tau) --j64;
+            if (j64 >= i) cnt64 += j64 - i + 1;
+        }
+        P->n_quartets_schwarz = cnt;
+        P->n_quartets_fp64 = precision == JK_FP64 ? P->n_quartets : cnt64;
+    }
+    // ---- R1 candidates for the real-space sums (Section 3.3)
+    {
+        std::map<double, double> kmax;  // pair exponent -> largest |K|
+        int lpmax = 0;
+        for (auto &s : P->spi) lpmax = std::max(lpmax, P->shells[s.I].l + P->shells[s.J].l);
+        for (auto &x : P->ppi) {
+            double &v = kmax[x.p];
+            v = std::max(v, std::fabs(x.K));
+        }
+        double rmax = 0;
+        for (auto &u : kmax)
+            for (auto &v : kmax) {
+                double r2 = realspace_r2(u.first, v.first, u.second * v.second, P->omega, c.ewald_R, 2 * lpmax);
+                if (r2 > 0) rmax = std::max(rmax, std::sqrt(r2));
+            }
+        P->r1_max = rmax;
+        double half = 0;
+        for (int s = 0; s < 8; ++s) {
+            double v[3];
+            lat_point(L, (s & 1) ? 0.5 : -0.5, (s & 2) ? 0.5 : -0.5, (s & 4) ? 0.5 : -0.5, v);
+            half = std::max(half, std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+        }
+        double zero[3] = {0, 0, 0};
+        std::vector<std::array<double, 4>> cand;
+        enumerate_sphere(L, P->Finv, zero, rmax + half + 1e-9, [&](int, int, int, const double *R) {
+            cand.push_back({R[0], R[1], R[2], std::sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2])});
+        });
+        std::sort(cand.begin(), cand.end(), [](const std::array<double, 4> &a, const std::array<double, 4> &b) { return a[3] < b[3]; });
+        for (auto &v : cand)
+            for (int k = 0; k < 4; ++k) P->r1.push_back(v[k]);
+    }
+    // ---- reciprocal vectors: half space, |G| < G_max from Eq.
+    // pbc_eri_reciprocal_cutoff_definition written per pair density,
+    // (4 pi/(V Kmin^2)) e^{-G^2/4w^2} s(G)^2 max(1,G)^{2Lp} > delta_K,
+    // s(G) = max_pairs |K| (pi/p)^{3/2} e^{-G^2/4p}.
+    {
+        double B[9];
+        for (int i = 0; i < 9; ++i) B[i] = 2.0 * kPi * P->Finv[i];  // rows b_i
+        double kmin = 1e300;
+        for (int a = -2; a <= 2; ++a)
+            for (int b = -2; b <= 2; ++b)
+                for (int d = -2; d <= 2; ++d) {
+                    if (!a && !b && !d) continue;
+                    double g[3];
+                    lat_point(B, a, b, d, g);
+                    kmin = std::min(kmin, std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+                }
+        std::map<double, double> amp;  // p -> max |K| (pi/p)^{3/2}
+        int lpmax = 0;
+        for (auto &s : P->spi) lpmax = std::max(lpmax, P->shells[s.I].l + P->shells[s.J].l);
+        for (auto &x : P->ppi) {
+            double &v = amp[x.p];
+            v = std::max(v, std::fabs(x.K) * std::pow(kPi / x.p, 1.5));
+        }
+        double pref = 4.0 * kPi / (V * kmin * kmin);
+        double gmax = 0;
+        for (double G = kmin * 0.5; G < 60.0 * P->omega + 50.0; G += 0.002 + 0.002 * G) {
+            double s = 0;
+            for (auto &u : amp) s = std::max(s, u.second * std::exp(-G * G / (4.0 * u.first)));
+            double wgt = pref * std::exp(-G * G / (4.0 * P->omega * P->omega)) * s * s * std::pow(std::max(1.0, G), 2 * lpmax);
+            if (wgt > c.ewald_K) gmax = G;
+        }
+        P->g_max = gmax;
+        double zero[3] = {0, 0, 0}, BT[9], BF[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) BT[3 * i + j] = B[3 * j + i];
+        inv3(BT, BF);
+        std::vector<std::array<double, 4>> gl;
+        enumerate_sphere(B, BF, zero, gmax, [&](int a, int b, int d, const double *g) {
+            bool pos = a > 0 || (a == 0 && (b > 0 || (b == 0 && d > 0)));
+            if (!pos) return;
+            double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+            double w = std::exp(-g2 / (4.0 * P->omega * P->omega)) / g2;
+            gl.push_back({g[0], g[1], g[2], std::sqrt(8.0 * kPi * w / V)});
+        });
+        std::sort(gl.begin(), gl.end(), [](const std::array<double, 4> &a, const std::array<double, 4> &b) {
+            return a[0] * a[0] + a[1] * a[1] + a[2] * a[2] < b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        });
+        for (auto &v : gl)
+            for (int k = 0; k < 4; ++k) P->gvec.push_back(v[k]);
+    }
+    *out = P;
+    return JK_OK;
+}
+
+// Device side of plan creation: uploads, Boys tables, workspace, overlap.
+int finish_plan_device(Plan *P)
+{
+    if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+    int rc;
+    size_t &b = P->device_bytes;
+    if ((rc = upload(P->shells, &P->d_shells, b)) || (rc = upload(P->spi, &P->d_spi, b)) || (rc = upload(P->ppi, &P->d_ppi, b)) ||
+        (rc = upload(P->spair, &P->d_spair, b)) || (rc = upload(P->spi_order, &P->d_spi_order, b)) ||
+        (rc = upload(P->r1, &P->d_r1, b)) || (rc = upload(P->gvec, &P->d_gvec, b)) || (rc = upload(P->compf, &P->d_compf, b)))
+        return rc;
+    std::vector<double> tab;
+    boys_table(JK_BOYS_MCOL, JK_BOYS_NPTS, JK_BOYS_INV_STEP, tab);
+    std::vector<float> tabf(tab.begin(), tab.end());
+    if ((rc = upload(tab, &P->d_boys, b)) || (rc = upload(tabf, &P->d_boys_f, b))) return rc;
+    std::vector<double> g0 = {0.0, 0.0, 0.0, 1.0};
+    if ((rc = upload(g0, &P->d_g0, b))) return rc;
+    std::vector<double> zeros((size_t)P->nbf * P->nbf, 0.0);
+    if ((rc = upload(zeros, &P->d_S, b))) return rc;
+    if ((rc = alloc_ws(P))) return rc;
+    if (cublasCreate(&P->blas) != CUBLAS_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cublasCreate failed");
+    if ((rc = compute_overlap_raw(P, 0))) return rc;
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(JK_ERR_CUDA, "plan setup kernels failed");
+    return JK_OK;
+}
+
+void destroy_plan(Plan *P)
+{
+    if (!P) return;
+    cudaSetDevice(P->device);
+    void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
+                    P->d_g0, P->d_compf, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
+                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (P->blas) cublasDestroy(P->blas);
+    P->timer.destroy();
+    delete P;
+}
+
+// Point-charge Ewald energy (Eq. nuclear_repulsion_energy) on the host.
+double ewald_point_charges_host(const double *lat, int n, const double *q, const double *xyz, double omega, double delta)
+{
+    double LT[9], Finv[9], B[9], BF[9], BT[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) LT[3 * i + j] = lat[3 * j + i];
+    inv3(LT, Finv);
+    double V = std::fabs(lat[0] * (lat[4] * lat[8] - lat[5] * lat[7]) - lat[1] * (lat[3] * lat[8] - lat[5] * lat[6]) +
+                         lat[2] * (lat[3] * lat[7] - lat[4] * lat[6]));
+    for (int i = 0; i < 9; ++i) B[i] = 2.0 * kPi * Finv[i];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) BT[3 * i + j] = B[3 * j + i];
+    inv3(BT, BF);
+    // radii of Eqs. nuclear_repulsion_energy_real_cutoff / _reciprocal_cutoff, solved by bisection
+    auto solve = [](auto f) {
+        double lo = 1e-3, hi = 1.0;
+        while (f(hi) > 0) hi *= 2;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            (f(mid) > 0 ? lo : hi) = mid;
+        }
+        return hi;
+    };
+    double rb = solve([&](double r) { return 2.0 / std::sqrt(kPi) * std::exp(-omega * omega * r * r) / (r * r) - delta; });
+    double kb = solve([&](double k) { return 4.0 * kPi / V * std::exp(-k * k / (4.0 * omega * omega)) / (k * k) - delta; });
+    double E = 0;
+    for (int a = 0; a < n; ++a)
+        for (int bb = a; bb < n; ++bb) {
+            double d[3] = {xyz[3 * a] - xyz[3 * bb], xyz[3 * a + 1] - xyz[3 * bb + 1], xyz[3 * a + 2] - xyz[3 * bb + 2]};
+            double nd[3] = {-d[0], -d[1], -d[2]};
+            double real = 0, recip = 0;
+            enumerate_sphere(lat, Finv, nd, rb, [&](int i, int j, int k, const double *R) {
+                if (a == bb && !i && !j && !k) return;
+                double x = d[0] + R[0], y = d[1] + R[1], z = d[2] + R[2];
+                double r = std::sqrt(x * x + y * y + z * z);
+                real += std::erfc(omega * r) / r;
+            });
+            double zero[3] = {0, 0, 0};
+            enumerate_sphere(B, BF, zero, kb, [&](int i, int j, int k, const double *G) {
+                if (!i && !j && !k) return;
+                double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+                recip += std::exp(-g2 / (4.0 * omega * omega)) / g2 * std::cos(G[0] * d[0] + G[1] * d[1] + G[2] * d[2]);
+            });
+            double term = 4.0 * kPi / V * recip - kPi / (V * omega * omega) + real;
+            if (a == bb)
+                E += 0.5 * q[a] * q[a] * (term - 2.0 * omega / std::sqrt(kPi));
+            else
+                E += q[a] * q[bb] * term;
+        }
+    return E;
+}
+
+}  // namespace jk

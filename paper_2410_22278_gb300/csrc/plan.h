@@ -1,0 +1,108 @@
+// Host-side plan: built once per geometry (Section 3.1), then immutable.
+#pragma once
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/jk.h"
+#include "jk_internal.h"
+
+namespace jk {
+
+// thread-local last error; returns the status for convenience
+int fail(int status, const std::string &msg);
+
+struct ClassRange {
+    int la, lb;
+    int b0, b1;  // spi index range
+};
+
+struct Workspace {
+    double *Dp = nullptr;     // D scaled by component factors
+    double *X = nullptr;      // real-space J accumulator
+    double *Y = nullptr;      // real-space K accumulator
+    double *JLR = nullptr;    // reciprocal J (raw components)
+    double *KLR = nullptr;    // reciprocal K (raw components)
+    double *T1 = nullptr;     // n x n temporaries
+    double *T2 = nullptr;
+    double *M = nullptr;      // structure-factor chunk [2*gc][n][n]
+    double *Z = nullptr;      // D * M chunk, stacked
+    double *rho = nullptr;    // [2*gc] density structure factors
+    double *dmax = nullptr;   // [nshell*nshell] max |D'| per shell block
+    double *scal = nullptr;   // small scalars (traces, energies)
+    unsigned *err = nullptr;  // device check word
+    int gc = 0;               // G vectors per chunk
+    size_t bytes = 0;
+};
+
+// CUDA events bracketing the phases of one build (see jk_build_times)
+struct PhaseTimer {
+    static constexpr int kPhases = 7;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<int, int>>> marks;  // phase, (start event, end event)
+    int next = 0;
+    int launches[kPhases] = {0};
+    cudaStream_t st = nullptr;
+    void begin(cudaStream_t s);
+    int start(int phase);
+    void stop(int phase, int ev_start, int nlaunch);
+    void destroy();
+};
+
+struct Plan {
+    int device = 0;
+    jk_precision precision = JK_FP64;
+    int nbf = 0, nshell = 0;
+    double omega = 0, volume = 0, g_max = 0, r1_max = 0;
+    jk_cutoffs cut{};
+    double L[9]{}, Finv[9]{};
+    // host copies
+    std::vector<ShellRec> shells;
+    std::vector<SpiRec> spi;
+    std::vector<PpiRec> ppi;
+    std::vector<SpairRec> spair;
+    std::vector<int> spi_order;
+    std::vector<ClassRange> classes;
+    std::vector<double> r1;    // [nr1][4]
+    std::vector<double> gvec;  // [ng][4]
+    std::vector<double> compf;
+    std::vector<int> spair_class_off;  // shell pairs grouped by class: [JK_NCLASS_MAX+1]
+    long long n_ord_shell_pairs = 0, n_ord_prim_pairs = 0, n_ord_local_pairs = 0;
+    long long n_shell_pairs = 0, n_quartets = 0, n_quartets_schwarz = 0, n_quartets_fp64 = 0;
+    double mixed_tau = 0;
+    // device arrays
+    ShellRec *d_shells = nullptr;
+    SpiRec *d_spi = nullptr;
+    PpiRec *d_ppi = nullptr;
+    SpairRec *d_spair = nullptr;
+    int *d_spi_order = nullptr;
+    double *d_boys = nullptr;
+    float *d_boys_f = nullptr;
+    double *d_r1 = nullptr;
+    double *d_gvec = nullptr;
+    double *d_g0 = nullptr;  // one G = 0 entry with unit weight (overlap)
+    double *d_compf = nullptr;
+    double *d_S = nullptr;  // raw-component overlap over the pair list
+    size_t device_bytes = 0;
+    Workspace ws;
+    PhaseTimer timer;
+    cublasHandle_t blas = nullptr;
+    std::mutex build_mu;
+    PlanDev dev() const;
+};
+
+int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double omega, const jk_cutoffs *cut,
+               jk_precision precision, int device, Plan **out);
+void destroy_plan(Plan *p);
+int run_build(Plan *p, const double *D, double *J, double *K, cudaStream_t st);
+int compute_overlap_raw(Plan *p, cudaStream_t st);
+int build_times(Plan *p, double *ms, int *launches, int n);
+
+// host helpers shared by plan.cu and api.cu
+void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out);
+double ewald_point_charges_host(const double *lat, int n, const double *q, const double *xyz, double omega, double delta);
+
+}  // namespace jk
