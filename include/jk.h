@@ -156,6 +156,11 @@ int jk_energy(const jk_plan *plan, const double *D, const double *J, const doubl
  * n = number of slots the caller provides (<= 7 used). */
 int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
 
+/* Work counters of the most recent jk_build (waits for it to finish):
+ * counts[0] unique image quartets evaluated in real space in FP64,
+ * counts[1] those evaluated in FP32 (mixed precision only).  n <= 4. */
+int jk_build_counts(jk_plan *plan, long long *counts, int n);
+
 /* Gamma overlap over the plan's pair list (Eq. pbc_overlap_formula),
  * written to the device pointer S (nbf*nbf FP64); stream-ordered. */
 int jk_overlap(const jk_plan *plan, double *S, void *cuda_stream);
@@ -193,6 +198,13 @@ int jk_wait(jk_server *srv, long long ticket, int timeout_ms, int *build_status,
 void jk_server_destroy(jk_server *srv);
 
 /* ---- diagnostics ---------------------------------------------------------- */
+
+/* Measurement utility (not part of a build): FMA throughput of the current
+ * device in TFLOP/s (2 flops per FMA), FP64 if fp64 != 0 else FP32, from a
+ * kernel of independent FMA chains timed with CUDA events.  The ALU
+ * rooflines of the quartet kernels are reported against these. */
+int jk_microbench_fma(int fp64, double *tflops);
+
 const char *jk_status_string(int status);
 const char *jk_last_error(void);
 

@@ -1019,3 +1019,98 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Timing sample for the CPU baseline: the same code paths as orc_jk_rows
+ * on a bounded subset of the work of a full build.
+ *   real space: every bra_stride-th ordered local pair as the bra, against
+ *               every ket local pair (digested into scratch J and K);
+ *   reciprocal: ng_sample half-space G vectors: all pair transforms, the
+ *               Coulomb contraction and the exchange contraction of one AO
+ *               row.
+ * out[0] seconds of the real-space sample, out[1] bra pairs sampled,
+ * out[2] ordered local pairs in total, out[3] seconds per G of the pair
+ * transforms, out[4] seconds per G per AO row of the contractions,
+ * out[5] half-space G vectors in the oracle's list, out[6] nbf.          */
+void orc_jk_sample(const orc_basis *bs, const double *D, int bra_stride, int ng_sample, double *out)
+{
+    int *off = (int *)malloc(sizeof(int) * bs->nshell);
+    int nbf = ao_offsets(bs, off);
+    long n2 = (long)nbf * nbf;
+    lp_list Lall = build_lps(bs, NULL, 0);
+    double *jacc = (double *)calloc(n2, sizeof(double)), *kacc = (double *)calloc(n2, sizeof(double));
+    long nb = 0;
+    double t0 = omp_get_wtime();
+#pragma omp parallel
+    {
+        double blk[6 * 6 * 6 * 6];
+#pragma omp for schedule(dynamic, 1) reduction(+ : nb)
+        for (long ii = 0; ii < Lall.n; ii += bra_stride) {
+            nb++;
+            const orc_lp *x = &Lall.v[ii];
+            for (long j = 0; j < Lall.n; j++) {
+                const orc_lp *y = &Lall.v[j];
+                int la = bs->l[x->I], lb = bs->l[x->J], lc = bs->l[y->I], ld = bs->l[y->J];
+                rs_ctx c;
+                real_space_R(bs, x, y, la + lb + lc + ld, 1, &c);
+                int na = ncart(la), nbb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
+                memset(blk, 0, sizeof(double) * na * nbb * nc * nd);
+                contract_block(bs, x, y, &c, blk);
+                for (int ia = 0; ia < na; ia++)
+                    for (int ib = 0; ib < nbb; ib++)
+                        for (int ic = 0; ic < nc; ic++)
+                            for (int id = 0; id < nd; id++) {
+                                double v = blk[((ia * nbb + ib) * nc + ic) * nd + id];
+                                long mu = off[x->I] + ia, nu = off[x->J] + ib, lam = off[y->I] + ic, sig = off[y->J] + id;
+#pragma omp atomic
+                                jacc[mu * nbf + nu] += v * D[lam * nbf + sig];
+#pragma omp atomic
+                                kacc[mu * nbf + sig] += v * D[nu * nbf + lam];
+                            }
+            }
+        }
+    }
+    out[0] = omp_get_wtime() - t0;
+    out[1] = (double)nb;
+    out[2] = (double)Lall.n;
+    g_list GL = half_space_G(bs->lat, oracle_gmax(bs));
+    double complex *M = (double complex *)malloc(sizeof(double complex) * n2);
+    double complex *T = (double complex *)malloc(sizeof(double complex) * nbf);
+    double tft = 0, tcon = 0;
+    int ns = ng_sample < GL.n ? ng_sample : (int)GL.n;
+    for (int s = 0; s < ns; s++) {
+        const double *G = GL.g + 3 * (long)(s * (GL.n / (ns > 0 ? ns : 1)));
+        double t1 = omp_get_wtime();
+        memset(M, 0, sizeof(double complex) * n2);
+        for (long q = 0; q < Lall.n; q++) add_pair_ft(bs, &Lall.v[q], off, G, nbf, M);
+        double t2 = omp_get_wtime();
+        double complex rhoD = 0;
+        for (long a = 0; a < n2; a++) rhoD += D[a] * M[a];
+        long mu = 0;
+        for (int nu = 0; nu < nbf; nu++) jacc[nu] += creal(conj(M[mu * nbf + nu]) * rhoD);
+        for (int s2 = 0; s2 < nbf; s2++) {
+            double complex t = 0;
+            for (int l = 0; l < nbf; l++) t += conj(M[mu * nbf + l]) * D[(long)l * nbf + s2];
+            T[s2] = t;
+        }
+        for (int nu = 0; nu < nbf; nu++) {
+            double complex k = 0;
+            for (int s2 = 0; s2 < nbf; s2++) k += T[s2] * M[(long)s2 * nbf + nu];
+            kacc[nu] += creal(k);
+        }
+        double t3 = omp_get_wtime();
+        tft += t2 - t1;
+        tcon += t3 - t2;
+    }
+    out[3] = ns ? tft / ns : 0;
+    out[4] = ns ? tcon / ns : 0;
+    out[5] = (double)GL.n;
+    out[6] = (double)nbf;
+    free(M);
+    free(T);
+    free(GL.g);
+    free(jacc);
+    free(kacc);
+    free(Lall.v);
+    free(off);
+}

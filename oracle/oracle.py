@@ -82,6 +82,7 @@ def lib():
             _lib.orc_ewald_point_charges.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double]
             _lib.orc_ewald_point_charges.restype = ctypes.c_double
             _lib.orc_num_threads.restype = ctypes.c_int
+            _lib.orc_jk_sample.argtypes = [B, dp, ctypes.c_int, ctypes.c_int, dp]
     return _lib
 
 
@@ -257,6 +258,22 @@ def density(cell) -> np.ndarray:
     from synthcells import density_from_overlap
 
     return density_from_overlap(cell.orbital_guess(), overlap(cell))
+
+
+def jk_sample_seconds(cell, D, bra_stride, ng_sample=1, delta=ORACLE_DELTA, margin=ORACLE_MARGIN):
+    """Time a bounded sample of a full J+K build with the oracle's own code
+    paths and extrapolate: (estimated seconds of a full build, detail dict).
+    Real space: every bra_stride-th ordered local pair against all; reciprocal:
+    ng_sample G vectors (pair transforms, Coulomb and one exchange row)."""
+    b = Basis(cell, delta=delta, margin=margin)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    out = np.zeros(7)
+    lib().orc_jk_sample(b.ref(), _dp(D), int(bra_stride), int(ng_sample), _dp(out))
+    t_real, nb, nlp, t_ft, t_row, ng, nbf = out
+    full = t_real * nlp / max(nb, 1) + ng * (t_ft + t_row * nbf)
+    detail = dict(real_s=t_real, bra_sampled=int(nb), local_pairs=int(nlp), ft_s_per_G=t_ft, row_s_per_G=t_row,
+                  n_g=int(ng), nbf=int(nbf), sample_s=t_real + ng_sample * (t_ft + t_row))
+    return full, detail
 
 
 def num_threads() -> int:

@@ -159,6 +159,13 @@ int jk_build_times(jk_plan *plan, double *ms, int *launches, int n)
     return jk::build_times(plan->p, ms, launches, n);
 }
 
+int jk_build_counts(jk_plan *plan, long long *counts, int n)
+{
+    if (!plan || !counts || n < 0) return fail(JK_ERR_INVALID, "bad arguments");
+    std::lock_guard<std::mutex> g(plan->p->build_mu);
+    return jk::build_counts(plan->p, counts, n);
+}
+
 int jk_build_host(jk_plan *plan, const double *Dh, double *Jh, double *Kh, void *cuda_stream)
 {
     if (!plan || !Dh) return fail(JK_ERR_INVALID, "plan or D is NULL");

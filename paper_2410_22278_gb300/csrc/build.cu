@@ -200,6 +200,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     cudaMemsetAsync(w.JLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.KLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(w.cnt, 0, 4 * sizeof(unsigned long long), st);
     int rc;
     if ((rc = cuda_check("prologue"))) return rc;
     tm.stop(0, ev, mixed ? 2 : 1);
@@ -228,14 +229,17 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             if (!mixed) {
                 a.mode = 0;
                 a.fp32 = false;
+                a.cnt = w.cnt;
                 launch_real(cb, ck, a);
                 nreal += 1;
             } else {
                 a.mode = 1;
                 a.fp32 = false;
+                a.cnt = w.cnt;
                 launch_real(cb, ck, a);
                 a.mode = 2;
                 a.fp32 = true;
+                a.cnt = w.cnt + 1;
                 launch_real(cb, ck, a);
                 nreal += 2;
             }
@@ -266,9 +270,14 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
         }
         if (K) {
             ev = tm.start(4);
+            // FP64 path: native DGEMM; mixed path: DGEMM with cuBLAS's fixed-point
+            // FP64 emulation on the tensor cores (FP64-accurate products)
+            BLAS_OK(cublasSetMathMode(P->blas, mixed ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH : CUBLAS_DEFAULT_MATH));
+            if (mixed) BLAS_OK(cublasSetEmulationStrategy(P->blas, CUBLAS_EMULATION_STRATEGY_EAGER));
             BLAS_OK(cublasDgemmStridedBatched(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, w.Dp, n, 0, w.M, n, (long long)n2,
                                               &zero, w.Z, m2 * n, n, m2));
             BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, m2 * n, &one, w.M, n, w.Z, m2 * n, &one, w.KLR, n));
+            BLAS_OK(cublasSetMathMode(P->blas, CUBLAS_DEFAULT_MATH));
             tm.stop(4, ev, 2);
         }
     }
@@ -286,6 +295,16 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     tm.stop(5, ev, K ? 4 : 2);
     tm.stop(6, ev_all, 0);
     return cuda_check("epilogue");
+}
+
+int build_counts(Plan *P, long long *counts, int n)
+{
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (P->timer.next > 0 && cudaEventSynchronize(P->timer.pool[P->timer.next - 1]) != cudaSuccess)
+        return fail(JK_ERR_CUDA, "build did not finish");
+    if (cudaMemcpy(h, P->ws.cnt, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(JK_ERR_CUDA, "count copy failed");
+    for (int i = 0; i < n && i < 4; ++i) counts[i] = (long long)h[i];
+    return JK_OK;
 }
 
 int build_times(Plan *P, double *ms, int *launches, int n)

@@ -37,6 +37,8 @@ struct SpiRec {      // one unique shell-pair image
     float w;         // orbit weight: 0.5 for (I, I, R = 0), else 1
     int spair;       // index of the unique shell pair (I, J)
     double Q;        // Schwarz estimate (Eq. pbc_eri_cauchy_schwarz_cutoff_definition, summed over primitives)
+    float Pc[3];     // centre of the image's largest primitive pair
+    float ext;       // max |P_i - Pc| over its primitive pairs
 };
 
 struct PpiRec {      // one local primitive pair
@@ -45,7 +47,16 @@ struct PpiRec {      // one local primitive pair
     double PB[3];    // P - (B + R)
     double p;        // a + b
     double K;        // c_a c_b exp(-ab/p |A - B - R|^2), normalised coefficients
-    double pad;
+    double pad;      // 1/p
+};
+
+struct PpiF {        // single-precision copy of a local primitive pair (FP32 kernels, screening)
+    float P[3];
+    float PA[3];
+    float PB[3];
+    float p;
+    float K;
+    float pad;       // 1/p
 };
 
 struct SpairRec {    // unique shell pair (I, J) with its images [spi0, spi0 + nspi)
@@ -62,7 +73,9 @@ struct PlanDev {
     const int *spi_order;        // spi indices grouped by shell pair (for the reciprocal build)
     const double *boys;          // [JK_BOYS_NPTS][JK_BOYS_MCOL]
     const float *boys_f;
+    const PpiF *ppf;
     const double *r1;            // [nr1][4]: x, y, z, |R|, sorted by |R|
+    const float *r1f;            // the same in single precision
     int nr1;
     const double *gvec;          // [ng][4]: Gx, Gy, Gz, sqrt(8 pi w(G) / V)
     int ng;
@@ -70,6 +83,7 @@ struct PlanDev {
     double L[9];                 // lattice rows a, b, c
     double Finv[9];              // fractional coordinates f = Finv * r
     double omega, inv_omega2;
-    double ewald_R;              // delta_Ewald-R
+    double ewald_R;              // delta_Ewald-R as given
+    float log_ewald_R;           // ln of the per-term threshold used inside the real-space sums
     double volume;
 };

@@ -26,16 +26,6 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi52 = 34.986836655249725;  // 2 pi^{5/2}
 constexpr int kRealThreads = 128;
 
-template <typename T>
-struct Prec;
-template <>
-struct Prec<double> {
-    __device__ static const double *tab(const PlanDev &pl) { return pl.boys; }
-};
-template <>
-struct Prec<float> {
-    __device__ static const float *tab(const PlanDev &pl) { return pl.boys_f; }
-};
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -44,98 +34,142 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Attenuated seeds s_m = (-2 alpha)^m F_m(alpha X^2) - c_w (-2 alpha_w)^m F_m(alpha_w X^2).
+// Attenuated seeds s_m = (-2 alpha)^m F_m(alpha X^2) - c_w (-2 alpha_w)^m F_m(alpha_w X^2)
+// = (-2 alpha)^m G_m(alpha X^2, c_w)  (see boys_attenuated).
 template <int L>
 __device__ __forceinline__ void seeds(double x2, double alpha, double aw, double cw, const PlanDev &pl, double *s)
 {
-    double F1[L + 1], F2[L + 1];
-    boys<L>(alpha * x2, pl.boys, F1);
-    boys<L>(aw * x2, pl.boys, F2);
-    double f1 = 1.0, f2 = cw;
+    (void)aw;
+    double G[L + 1];
+    boys_attenuated<L, double>(alpha * x2, cw, pl.boys, G);
+    double f = 1.0;
 #pragma unroll
     for (int m = 0; m <= L; ++m) {
-        s[m] = f1 * F1[m] - f2 * F2[m];
-        f1 *= -2.0 * alpha;
-        f2 *= -2.0 * aw;
+        s[m] = f * G[m];
+        f *= -2.0 * alpha;
     }
 }
-// Single precision unless the two terms nearly cancel (c_w close to 1),
-// where the seed is formed in double and rounded once.
+// Single precision unless c_w is close to 1 (the integration interval
+// [c_w, 1] is short and the table branch would lose bits), where the seed is
+// formed in double and rounded once.
 template <int L>
-__device__ __forceinline__ void seeds(double x2, double alpha, double aw, double cw, const PlanDev &pl, float *s)
+__device__ __forceinline__ void seeds(float x2, float alpha, float aw, float cw, const PlanDev &pl, float *s)
 {
-    if (cw > 0.85) {
+    if (cw > 0.85f) {
         double sd[L + 1];
-        seeds<L>(x2, alpha, aw, cw, pl, sd);
+        seeds<L>((double)x2, (double)alpha, (double)aw, (double)cw, pl, sd);
 #pragma unroll
         for (int m = 0; m <= L; ++m) s[m] = (float)sd[m];
         return;
     }
-    float F1[L + 1], F2[L + 1];
-    boys<L>((float)(alpha * x2), pl.boys_f, F1);
-    boys<L>((float)(aw * x2), pl.boys_f, F2);
-    float f1 = 1.0f, f2 = (float)cw;
-    const float ma = (float)(-2.0 * alpha), mw = (float)(-2.0 * aw);
+    float G[L + 1];
+    boys_attenuated<L, float>(alpha * x2, cw, pl.boys_f, G);
+    float f = 1.0f;
 #pragma unroll
     for (int m = 0; m <= L; ++m) {
-        s[m] = f1 * F1[m] - f2 * F2[m];
-        f1 *= ma;
-        f2 *= mw;
+        s[m] = f * G[m];
+        f *= -2.0f * alpha;
     }
 }
 
-// Contracted real-space block V[((a*NB+b)*NC+c)*ND+d] of one pair of shell-pair images.
+// Pair data in the kernel's working precision.
+template <typename T>
+struct PairT {
+    T P[3], PA[3], PB[3], p, ip, K;
+};
+__device__ __forceinline__ void load_pair(const PlanDev &pl, int k, const PpiF &, PairT<double> &o)
+{
+    const PpiRec x = pl.ppi[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o.P[a] = x.P[a];
+        o.PA[a] = x.PA[a];
+        o.PB[a] = x.PB[a];
+    }
+    o.p = x.p;
+    o.ip = x.pad;
+    o.K = x.K;
+}
+__device__ __forceinline__ void load_pair(const PlanDev &, int, const PpiF &f, PairT<float> &o)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o.P[a] = f.P[a];
+        o.PA[a] = f.PA[a];
+        o.PB[a] = f.PB[a];
+    }
+    o.p = f.p;
+    o.ip = f.pad;
+    o.K = f.K;
+}
+__device__ __forceinline__ double lat_at(const PlanDev &pl, int k, double) { return pl.r1[k]; }
+__device__ __forceinline__ float lat_at(const PlanDev &pl, int k, float) { return pl.r1f[k]; }
+
+// Contracted real-space block V[((a*NB+b)*NC+c)*ND+d] of one pair of
+// shell-pair images.  The sphere of Eq. pbc_eri_real_cutoff_implementation
+// and the R1 candidate tests are evaluated in single precision for both
+// kernels (they only decide which terms to form); the terms themselves are
+// formed in T.
 template <int LA, int LB, int LC, int LD, typename T>
 __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk, T *V)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int L = LA + LB + LC + LD, LAB = LA + LB, LCD = LC + LD;
     constexpr int NTA = LAB + 1, NTC = LCD + 1, D = L + 1;
+    const float iw2 = (float)pl.inv_omega2;
     for (int i = 0; i < sb.npp; ++i) {
-        const PpiRec x = pl.ppi[sb.pp0 + i];
+        const PpiF xf = pl.ppf[sb.pp0 + i];
+        PairT<T> x;
+        load_pair(pl, sb.pp0 + i, xf, x);
         T Ea[3][(LA + 1) * (LB + 1) * NTA];
-        const T oo2p = T(0.5 / x.p);
+        const T oo2p = T(0.5) * x.ip;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) herm_E<LA, LB, T>(T(x.PA[k]), T(x.PB[k]), oo2p, Ea[k]);
+        for (int k = 0; k < 3; ++k) herm_E<LA, LB, T>(x.PA[k], x.PB[k], oo2p, Ea[k]);
         for (int j = 0; j < sk.npp; ++j) {
-            const PpiRec y = pl.ppi[sk.pp0 + j];
-            const double p = x.p, q = y.p;
-            const double alpha = p * q / (p + q);
-            const double aw = 1.0 / (1.0 / p + 1.0 / q + pl.inv_omega2);
-            const double cw = sqrt(aw / alpha);
-            const double pref = kTwoPi52 / (p * q * sqrt(p + q)) * x.K * y.K;
-            // Eq. pbc_eri_real_cutoff_implementation with the Hermite growth margin
-            const double lg = log(fabs(pref) * (1.0 - cw) / pl.ewald_R);
-            if (lg <= 0.0) continue;
-            double r = sqrt(lg / aw);
-            r = sqrt((lg + L * log1p(2.0 * aw * r)) / aw);
-            r = sqrt((lg + L * log1p(2.0 * aw * r)) / aw);
-            const double r2 = r * r;
-            // minimum image of P - Q (Eq. lattice_image_min_norm)
-            double X0[3] = {x.P[0] - y.P[0], x.P[1] - y.P[1], x.P[2] - y.P[2]};
+            const PpiF yf = pl.ppf[sk.pp0 + j];
+            // ---- screening, single precision
+            const float ipf = xf.pad, iqf = yf.pad;
+            const float awf = 1.0f / (ipf + iqf + iw2);
+            const float cwf = sqrtf(awf * (ipf + iqf));
+            const float preff = 34.986836655249725f * xf.K * yf.K * ipf * iqf * rsqrtf(xf.p + yf.p);
+            const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
+            if (!(lg > 0.0f)) continue;
+            float r = sqrtf(lg / awf);
+            r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+            r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+            const float r2 = r * r;
+            PairT<T> y;
+            load_pair(pl, sk.pp0 + j, yf, y);
+            // minimum image of P - Q (Eq. lattice_image_min_norm), working precision
+            T X0[3] = {x.P[0] - y.P[0], x.P[1] - y.P[1], x.P[2] - y.P[2]};
             {
-                double f[3];
+                T f[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) f[a] = rint(pl.Finv[3 * a] * X0[0] + pl.Finv[3 * a + 1] * X0[1] + pl.Finv[3 * a + 2] * X0[2]);
+                for (int a = 0; a < 3; ++a)
+                    f[a] = rint(T(pl.Finv[3 * a]) * X0[0] + T(pl.Finv[3 * a + 1]) * X0[1] + T(pl.Finv[3 * a + 2]) * X0[2]);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) X0[a] -= f[0] * pl.L[a] + f[1] * pl.L[3 + a] + f[2] * pl.L[6 + a];
+                for (int a = 0; a < 3; ++a) X0[a] -= f[0] * T(pl.L[a]) + f[1] * T(pl.L[3 + a]) + f[2] * T(pl.L[6 + a]);
             }
-            const double x0n = sqrt(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]);
+            const float x0n = sqrtf((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
             T Rs[D * D * D];
 #pragma unroll
             for (int k = 0; k < D * D * D; ++k) Rs[k] = T(0);
             bool any = false;
+            const T ip = x.ip, iq = y.ip;
+            const T aw = T(1) / (ip + iq + T(pl.inv_omega2));
+            const T alpha = T(1) / (ip + iq);
+            const T cw = sqrt(aw * (ip + iq));
             for (int c = 0; c < pl.nr1; ++c) {
-                const double4 rc = reinterpret_cast<const double4 *>(pl.r1)[c];
-                if (rc.w - x0n >= r) break;
-                const double Xx = X0[0] - rc.x, Xy = X0[1] - rc.y, Xz = X0[2] - rc.z;
-                const double x2 = Xx * Xx + Xy * Xy + Xz * Xz;
-                if (x2 >= r2) continue;
+                if (pl.r1f[4 * c + 3] - x0n >= r) break;
+                const T Xx = X0[0] - lat_at(pl, 4 * c, T(0)), Xy = X0[1] - lat_at(pl, 4 * c + 1, T(0)),
+                        Xz = X0[2] - lat_at(pl, 4 * c + 2, T(0));
+                const T x2 = Xx * Xx + Xy * Xy + Xz * Xz;
+                if ((float)x2 >= r2) continue;
                 any = true;
                 T s[L + 1];
                 seeds<L>(x2, alpha, aw, cw, pl, s);
                 T B[D * D * D];
-                herm_R<L, T>(s, T(Xx), T(Xy), T(Xz), B);
+                herm_R<L, T>(s, Xx, Xy, Xz, B);
 #pragma unroll
                 for (int t = 0; t <= L; ++t)
 #pragma unroll
@@ -145,11 +179,11 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             }
             if (!any) continue;
             T Ec[3][(LC + 1) * (LD + 1) * NTC];
-            const T oo2q = T(0.5 / q);
+            const T oo2q = T(0.5) * iq;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) herm_E<LC, LD, T>(T(y.PA[k]), T(y.PB[k]), oo2q, Ec[k]);
-            const T tp = T(pref);
-#pragma unroll
+            for (int k = 0; k < 3; ++k) herm_E<LC, LD, T>(y.PA[k], y.PB[k], oo2q, Ec[k]);
+            const T tp = T(kTwoPi52) * x.K * y.K * ip * iq / sqrt(x.p + y.p);
+            #pragma unroll
             for (int c = 0; c < NC; ++c)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
@@ -201,12 +235,42 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
     }
 }
 
-// mode: 0 every quartet; 1 only quartets whose density-weighted Schwarz
-// estimate is >= tau; 2 only those below tau.
+// Size estimate of the real-space block of a pair of images, for the
+// precision switch (not for screening): the sum over primitive quartets of
+// the Gaussian bound behind Eq. pbc_eri_real_cutoff_definition,
+// 2 pi^{5/2}/(pq sqrt(p+q)) |K K| (1 - c_w) exp(-alpha_w d^2), at the
+// distance d between the images' centres less their extents.
+__device__ __forceinline__ float quartet_estimate(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk)
+{
+    float X[3] = {sb.Pc[0] - sk.Pc[0], sb.Pc[1] - sk.Pc[1], sb.Pc[2] - sk.Pc[2]};
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = rintf((float)pl.Finv[3 * a] * X[0] + (float)pl.Finv[3 * a + 1] * X[1] + (float)pl.Finv[3 * a + 2] * X[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) X[a] -= f[0] * (float)pl.L[a] + f[1] * (float)pl.L[3 + a] + f[2] * (float)pl.L[6 + a];
+    const float d = fmaxf(0.0f, sqrtf(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
+    const float d2 = d * d, iw2 = (float)pl.inv_omega2;
+    float est = 0.0f;
+    for (int i = 0; i < sb.npp; ++i) {
+        const PpiF x = pl.ppf[sb.pp0 + i];
+        for (int j = 0; j < sk.npp; ++j) {
+            const PpiF y = pl.ppf[sk.pp0 + j];
+            const float aw = 1.0f / (x.pad + y.pad + iw2);
+            const float cw = sqrtf(aw * (x.pad + y.pad));
+            est += 34.986836655249725f * fabsf(x.K * y.K) * x.pad * y.pad * rsqrtf(x.p + y.p) * (1.0f - cw) * __expf(-aw * d2);
+        }
+    }
+    return est;
+}
+
+// mode: 0 every quartet; 1 only quartets whose density-weighted size
+// estimate is >= tau; 2 only those below tau.  cnt[0] counts the image
+// quartets evaluated, cnt[1] the primitive quartets inside the sphere.
 template <int LA, int LB, int LC, int LD, typename T>
 __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
                                                         double tau, const double *__restrict__ Dp, const double *__restrict__ dmax,
-                                                        double *__restrict__ X, double *__restrict__ Y)
+                                                        double *__restrict__ X, double *__restrict__ Y,
+                                                        unsigned long long *__restrict__ cnt)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     const int tile0 = b0 + blockIdx.x * kRealThreads;
@@ -228,19 +292,21 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
             jb[a * NB + b] = 0.0;
         }
     const double dIJ = mode ? dmax[sb.I * nsh + sb.J] : 0.0;
+    unsigned nq = 0;
     for (int kt = kbeg; kt < kend; ++kt) {
         const SpiRec sk = pl.spi[kt];
         bool valid = act && (!same || kt >= bra);
         if (valid && mode) {
             double dm = fmax(fmax(dIJ, dmax[sk.I * nsh + sk.J]), fmax(dmax[sb.J * nsh + sk.I], dmax[sb.I * nsh + sk.I]));
             dm = fmax(dm, fmax(dmax[sb.J * nsh + sk.J], dmax[sb.I * nsh + sk.J]));
-            const double bound = sb.Q * sk.Q * dm;
-            valid = (mode == 1) ? (bound >= tau) : (bound < tau);
+            const double est = (double)quartet_estimate(pl, sb, sk) * dm;
+            valid = (mode == 1) ? (est >= tau) : (est < tau);
         }
         T V[NA * NB * NC * ND];
 #pragma unroll
         for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = T(0);
         if (valid) quartet_block<LA, LB, LC, LD, T>(pl, sb, sk, V);
+        nq += valid;
         const double w = valid ? double(sb.w) * double(sk.w) * ((same && kt == bra) ? 0.5 : 1.0) : 0.0;
         const int aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
         // Coulomb, bra side: X_ij += 2w sum_kl V D_kl (held in registers over the ket loop)
@@ -320,6 +386,11 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
             for (int b = 0; b < NB; ++b)
                 if (jb[a * NB + b] != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, jb[a * NB + b]);
     }
+    // warp-aggregated count of the image quartets this launch evaluated
+    unsigned tot = nq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);
 }
 
 // Structure factors of one class of unique shell pairs for a chunk of G.

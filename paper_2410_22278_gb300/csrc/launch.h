@@ -14,6 +14,7 @@ struct RealLaunch {
     bool fp32;
     const double *Dp, *dmax;
     double *X, *Y;
+    unsigned long long *cnt;
     cudaStream_t st;
 };
 

@@ -161,4 +161,74 @@ __device__ __forceinline__ void boys(float T, const float *__restrict__ tab, flo
     }
 }
 
+// Top order only: F_L(T) for T < JK_BOYS_TMAX by the 7-term (double) or
+// 5-term (float) Taylor expansion about the nearest table point.
+template <int L>
+__device__ __forceinline__ double boys_top(double T, const double *__restrict__ tab)
+{
+    const int k = __double2int_rn(T * JK_BOYS_INV_STEP);
+    const double d = k * (1.0 / JK_BOYS_INV_STEP) - T;
+    const double *row = tab + k * JK_BOYS_MCOL + L;
+    double f = __ldg(row + 6) * (1.0 / 720.0);
+    f = f * d + __ldg(row + 5) * (1.0 / 120.0);
+    f = f * d + __ldg(row + 4) * (1.0 / 24.0);
+    f = f * d + __ldg(row + 3) * (1.0 / 6.0);
+    f = f * d + __ldg(row + 2) * 0.5;
+    f = f * d + __ldg(row + 1);
+    return f * d + __ldg(row + 0);
+}
+template <int L>
+__device__ __forceinline__ float boys_top(float T, const float *__restrict__ tab)
+{
+    const int k = __float2int_rn(T * float(JK_BOYS_INV_STEP));
+    const float d = k * (1.0f / JK_BOYS_INV_STEP) - T;
+    const float *row = tab + k * JK_BOYS_MCOL + L;
+    float f = __ldg(row + 4) * (1.0f / 24.0f);
+    f = fmaf(f, d, __ldg(row + 3) * (1.0f / 6.0f));
+    f = fmaf(f, d, __ldg(row + 2) * 0.5f);
+    f = fmaf(f, d, __ldg(row + 1));
+    return fmaf(f, d, __ldg(row + 0));
+}
+
+__device__ __forceinline__ double erfc_(double x) { return erfc(x); }
+__device__ __forceinline__ float erfc_(float x) { return erfcf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+
+// Range-separated Boys integrals G_m(T, c) = int_c^1 t^{2m} e^{-T t^2} dt,
+// m = 0..L.  The erfc-attenuated seed of the real-space sum is
+//   (-2a)^m F_m(aX^2) - c_w (-2a_w)^m F_m(a_w X^2) = (-2a)^m G_m(aX^2, c_w)
+// (substitute t -> t c_w in the second Boys integral), so the difference of
+// two nearly equal Boys values never has to be formed.  Integration by parts
+// gives (2m+1) G_m - 2T G_{m+1} = e^{-T} - c^{2m+1} e^{-c^2 T}:
+//   small T: G_L = F_L(T) - c^{2L+1} F_L(c^2 T) from the table, downward;
+//   large T: G_0 = sqrt(pi)/(2 sqrt T) (erfc(c sqrt T) - erfc(sqrt T)), upward.
+template <int L, typename T>
+__device__ __forceinline__ void boys_attenuated(T Tt, T c, const T *__restrict__ tab, T *G)
+{
+    const T c2 = c * c;
+    const T e1 = exp_(-Tt), e2 = exp_(-c2 * Tt);
+    if (Tt < T(L) + T(1.5)) {
+        T cp = c;  // c^{2m+1}
+#pragma unroll
+        for (int m = 0; m < L; ++m) cp *= c2;
+        G[L] = boys_top<L>(Tt, tab) - cp * boys_top<L>(c2 * Tt, tab);
+#pragma unroll
+        for (int m = L - 1; m >= 0; --m) {
+            cp /= c2;
+            G[m] = (T(2) * Tt * G[m + 1] + e1 - cp * e2) * (T(1) / T(2 * m + 1));
+        }
+    } else {
+        const T s = sqrt(Tt);
+        G[0] = T(0.88622692545275801365) / s * (erfc_(c * s) - erfc_(s));
+        T cp = c;
+        const T h = T(0.5) / Tt;
+#pragma unroll
+        for (int m = 0; m < L; ++m) {
+            G[m + 1] = (T(2 * m + 1) * G[m] - e1 + cp * e2) * h;
+            cp *= c2;
+        }
+    }
+}
+
 }  // namespace jk

@@ -111,6 +111,47 @@ static int pair_class(int la, int lb)  // la >= lb
     return la * (la + 1) / 2 + lb;
 }
 
+// Cartesian exponents of component k of a shell of momentum l (lx
+// descending, then ly descending)
+static void cart_exps(int l, int k, int *e)
+{
+    int n = 0;
+    for (int lx = l; lx >= 0; --lx)
+        for (int ly = l - lx; ly >= 0; --ly) {
+            if (n == k) {
+                e[0] = lx;
+                e[1] = ly;
+                e[2] = l - lx - ly;
+                return;
+            }
+            ++n;
+        }
+    e[0] = e[1] = e[2] = 0;
+}
+
+// Host copy of the E recursion (Eqs. E_recursion_i/j, E^{00}_0 = 1), used
+// only to bound structure factors when choosing the reciprocal cut-off.
+static void herm_E_host(int la, int lb, double PA, double PB, double oo2p, double E[3][3][5])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int t = 0; t < 5; ++t) E[i][j][t] = 0;
+    E[0][0][0] = 1;
+    for (int i = 0; i <= la; ++i)
+        for (int j = 0; j <= lb; ++j) {
+            if (!i && !j) continue;
+            for (int t = 0; t <= i + j; ++t) {
+                const double(*src)[5] = i > 0 ? &E[i - 1][j] : &E[i][j - 1];
+                const double X = i > 0 ? PA : PB;
+                const int top = i + j - 1;
+                double v = X * (*src)[t];
+                if (t > 0) v += oo2p * (*src)[t - 1];
+                if (t + 1 <= top) v += (t + 1) * (*src)[t + 1];
+                E[i][j][t] = v;
+            }
+        }
+}
+
 // F_m(T_k) table by the convergent series at the top order and downward
 // recursion, in long double.
 void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out)
@@ -168,6 +209,8 @@ PlanDev Plan::dev() const
     d.boys = d_boys;
     d.boys_f = d_boys_f;
     d.r1 = d_r1;
+    d.ppf = d_ppf;
+    d.r1f = d_r1f;
     d.nr1 = (int)(r1.size() / 4);
     d.gvec = d_gvec;
     d.ng = (int)(gvec.size() / 4);
@@ -177,6 +220,9 @@ PlanDev Plan::dev() const
     d.omega = omega;
     d.inv_omega2 = 1.0 / (omega * omega);
     d.ewald_R = cut.ewald_R;
+    // Eq. pbc_eri_real_cutoff_definition bounds one term; a matrix element
+    // sums 1e2-1e4 such terms, so the sphere is drawn at delta_Ewald-R / 100.
+    d.log_ewald_R = (float)std::log(cut.ewald_R * 1e-2);
     d.volume = volume;
     return d;
 }
@@ -214,6 +260,7 @@ static int alloc_ws(Plan *P)
               al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16);
     if (!ok) return fail(JK_ERR_OOM, "cudaMalloc failed for build workspace");
     if (cudaMalloc((void **)&w.err, sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
+    if (cudaMalloc((void **)&w.cnt, 4 * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
     cudaMemset(w.err, 0, sizeof(unsigned));
     w.bytes = bytes + sizeof(unsigned);
     return JK_OK;
@@ -266,7 +313,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     if (!(c.pair_cs > 0)) c.pair_cs = 1e-14;
     if (!(c.ewald_R > 0)) c.ewald_R = 1e-14;
     if (!(c.ewald_K > 0)) c.ewald_K = 1e-14;
-    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-9;
+    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-7;
     P->cut = c;
 
     // ---- shells, normalised coefficients, component factors
@@ -366,6 +413,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                         x.PB[k] = x.P[k] - B[k];
                     }
                     x.p = p;
+                    x.pad = 1.0 / p;
                     x.K = cn[sF.p0 + pa] * cn[sS.p0 + pb] * std::exp(-a * b / p * AB2);
                     pv.push_back(x);
                     Q += std::pow(2.0, 0.25) * std::fabs(x.K) * std::pow(kPi / p, 1.25);  // Eq. 445 per primitive
@@ -380,6 +428,13 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                 sr.n[2] = n[2];
                 sr.w = (I == J && n[0] == 0 && n[1] == 0 && n[2] == 0) ? 0.5f : 1.0f;
                 sr.Q = Q;
+                for (int k = 0; k < 3; ++k) sr.Pc[k] = (float)pv[0].P[k];
+                sr.ext = 0.f;
+                for (auto &x : pv) {
+                    double d2 = 0;
+                    for (int k = 0; k < 3; ++k) d2 += (x.P[k] - pv[0].P[k]) * (x.P[k] - pv[0].P[k]);
+                    sr.ext = std::max(sr.ext, (float)std::sqrt(d2));
+                }
                 spis.push_back(sr);
                 spi_ppis.push_back(std::move(pv));
             }
@@ -469,7 +524,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
         double rmax = 0;
         for (auto &u : kmax)
             for (auto &v : kmax) {
-                double r2 = realspace_r2(u.first, v.first, u.second * v.second, P->omega, c.ewald_R, 2 * lpmax);
+                double r2 = realspace_r2(u.first, v.first, u.second * v.second, P->omega, c.ewald_R * 1e-2, 2 * lpmax);
                 if (r2 > 0) rmax = std::max(rmax, std::sqrt(r2));
             }
         P->r1_max = rmax;
@@ -504,20 +559,60 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                     lat_point(B, a, b, d, g);
                     kmin = std::min(kmin, std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
                 }
-        std::map<double, double> amp;  // p -> max |K| (pi/p)^{3/2}
-        int lpmax = 0;
-        for (auto &s : P->spi) lpmax = std::max(lpmax, P->shells[s.I].l + P->shells[s.J].l);
-        for (auto &x : P->ppi) {
-            double &v = amp[x.p];
-            v = std::max(v, std::fabs(x.K) * std::pow(kPi / x.p, 1.5));
+        // per distinct pair exponent p: the largest amplitude |K| (pi/p)^{3/2}
+        // and, per (i, j, t), the largest |E^{ij}_t| over its pairs and axes, so
+        // that |rho_ab(G)| <= amp e^{-G^2/4p} prod_axis sum_t |E^{ij}_t| G^t
+        struct PBound {
+            double amp = 0;
+            double E[3][3][5] = {};
+            int la = 0, lb = 0;
+        };
+        std::map<double, PBound> pb;
+        for (auto &s : P->spi) {
+            const int la = P->shells[s.I].l, lb = P->shells[s.J].l;
+            for (int k = s.pp0; k < s.pp0 + s.npp; ++k) {
+                const PpiRec &x = P->ppi[k];
+                PBound &b = pb[x.p];
+                b.amp = std::max(b.amp, std::fabs(x.K) * std::pow(kPi / x.p, 1.5));
+                b.la = std::max(b.la, la);
+                b.lb = std::max(b.lb, lb);
+                for (int ax = 0; ax < 3; ++ax) {
+                    double E[3][3][5];
+                    herm_E_host(la, lb, x.PA[ax], x.PB[ax], 0.5 / x.p, E);
+                    for (int i = 0; i <= la; ++i)
+                        for (int j = 0; j <= lb; ++j)
+                            for (int t = 0; t <= i + j; ++t) b.E[i][j][t] = std::max(b.E[i][j][t], std::fabs(E[i][j][t]));
+                }
+            }
         }
-        double pref = 4.0 * kPi / (V * kmin * kmin);
-        double gmax = 0;
-        for (double G = kmin * 0.5; G < 60.0 * P->omega + 50.0; G += 0.002 + 0.002 * G) {
+        auto sbound = [&](double G) {
             double s = 0;
-            for (auto &u : amp) s = std::max(s, u.second * std::exp(-G * G / (4.0 * u.first)));
-            double wgt = pref * std::exp(-G * G / (4.0 * P->omega * P->omega)) * s * s * std::pow(std::max(1.0, G), 2 * lpmax);
-            if (wgt > c.ewald_K) gmax = G;
+            for (auto &u : pb) {
+                const PBound &b = u.second;
+                double poly = 0;  // max over component pairs of the product of axis polynomials
+                for (int a = 0; a < (b.la + 1) * (b.la + 2) / 2; ++a)
+                    for (int c = 0; c < (b.lb + 1) * (b.lb + 2) / 2; ++c) {
+                        int ea[3], eb[3];
+                        cart_exps(b.la, a, ea);
+                        cart_exps(b.lb, c, eb);
+                        double pr = 1;
+                        for (int ax = 0; ax < 3; ++ax) {
+                            double q = 0, gp = 1;
+                            for (int t = 0; t <= ea[ax] + eb[ax]; ++t, gp *= G) q += b.E[ea[ax]][eb[ax]][t] * gp;
+                            pr *= q;
+                        }
+                        poly = std::max(poly, pr);
+                    }
+                s = std::max(s, b.amp * std::exp(-G * G / (4.0 * u.first)) * poly);
+            }
+            return s;
+        };
+        // size of the largest reciprocal term at |G|: (4 pi / V) e^{-G^2/4w^2}/G^2 s(G)^2
+        double gmax = kmin;
+        for (double G = kmin; G < 40.0 * P->omega + 20.0; G += 0.005 + 0.002 * G) {
+            const double s = sbound(G);
+            const double wgt = 4.0 * kPi / V * std::exp(-G * G / (4.0 * P->omega * P->omega)) / (G * G) * s * s;
+            if (wgt > c.ewald_K * 1e-2) gmax = G;  // per-term bound; a matrix element sums many G
         }
         P->g_max = gmax;
         double zero[3] = {0, 0, 0}, BT[9], BF[9];
@@ -552,6 +647,22 @@ int finish_plan_device(Plan *P)
         (rc = upload(P->spair, &P->d_spair, b)) || (rc = upload(P->spi_order, &P->d_spi_order, b)) ||
         (rc = upload(P->r1, &P->d_r1, b)) || (rc = upload(P->gvec, &P->d_gvec, b)) || (rc = upload(P->compf, &P->d_compf, b)))
         return rc;
+    {
+        std::vector<PpiF> pf(P->ppi.size());
+        for (size_t i = 0; i < P->ppi.size(); ++i) {
+            const PpiRec &x = P->ppi[i];
+            for (int k = 0; k < 3; ++k) {
+                pf[i].P[k] = (float)x.P[k];
+                pf[i].PA[k] = (float)x.PA[k];
+                pf[i].PB[k] = (float)x.PB[k];
+            }
+            pf[i].p = (float)x.p;
+            pf[i].K = (float)x.K;
+            pf[i].pad = (float)(1.0 / x.p);
+        }
+        std::vector<float> r1f(P->r1.begin(), P->r1.end());
+        if ((rc = upload(pf, &P->d_ppf, b)) || (rc = upload(r1f, &P->d_r1f, b))) return rc;
+    }
     std::vector<double> tab;
     boys_table(JK_BOYS_MCOL, JK_BOYS_NPTS, JK_BOYS_INV_STEP, tab);
     std::vector<float> tabf(tab.begin(), tab.end());
@@ -571,9 +682,9 @@ void destroy_plan(Plan *P)
 {
     if (!P) return;
     cudaSetDevice(P->device);
-    void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
+    void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
                     P->d_g0, P->d_compf, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
-                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err};
+                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P->blas) cublasDestroy(P->blas);

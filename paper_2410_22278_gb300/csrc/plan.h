@@ -34,6 +34,7 @@ struct Workspace {
     double *dmax = nullptr;   // [nshell*nshell] max |D'| per shell block
     double *scal = nullptr;   // small scalars (traces, energies)
     unsigned *err = nullptr;  // device check word
+    unsigned long long *cnt = nullptr;  // [0] FP64 image quartets, [1] FP32 image quartets
     int gc = 0;               // G vectors per chunk
     size_t bytes = 0;
 };
@@ -77,6 +78,8 @@ struct Plan {
     ShellRec *d_shells = nullptr;
     SpiRec *d_spi = nullptr;
     PpiRec *d_ppi = nullptr;
+    PpiF *d_ppf = nullptr;
+    float *d_r1f = nullptr;
     SpairRec *d_spair = nullptr;
     int *d_spi_order = nullptr;
     double *d_boys = nullptr;
@@ -100,6 +103,7 @@ void destroy_plan(Plan *p);
 int run_build(Plan *p, const double *D, double *J, double *K, cudaStream_t st);
 int compute_overlap_raw(Plan *p, cudaStream_t st);
 int build_times(Plan *p, double *ms, int *launches, int n);
+int build_counts(Plan *p, long long *counts, int n);
 
 // host helpers shared by plan.cu and api.cu
 void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out);

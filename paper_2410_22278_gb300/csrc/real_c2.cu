@@ -12,9 +12,9 @@ static void go(const RealLaunch &a)
     if (nb <= 0 || nk <= 0) return;
     dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
     if (a.fp32)
-        k_real<LA, LB, LC, LD, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y);
+        k_real<LA, LB, LC, LD, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt);
     else
-        k_real<LA, LB, LC, LD, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y);
+        k_real<LA, LB, LC, LD, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt);
 }
 
 void launch_real_c2(int ck, const RealLaunch &a)

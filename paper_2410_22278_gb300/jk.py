@@ -32,9 +32,9 @@ JK_MIXED = 1
 
 # every symbol declared in include/jk.h
 EXPORTS = [
-    "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_energy",
+    "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_build_counts", "jk_energy",
     "jk_overlap", "jk_ewald_point_charges", "jk_server_create", "jk_submit", "jk_wait", "jk_server_destroy",
-    "jk_status_string", "jk_last_error",
+    "jk_status_string", "jk_last_error", "jk_microbench_fma",
 ]
 
 
@@ -94,6 +94,7 @@ def lib():
         L.jk_build.argtypes = [vp, vp, vp, vp, vp]
         L.jk_build_host.argtypes = [vp, dp, dp, dp, vp]
         L.jk_build_times.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        L.jk_build_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.jk_energy.argtypes = [vp, vp, vp, vp, dp, dp, vp]
         L.jk_overlap.argtypes = [vp, vp, vp]
         L.jk_ewald_point_charges.argtypes = [ctypes.POINTER(jk_cell), ctypes.c_int, dp, dp, ctypes.c_double,
@@ -107,6 +108,7 @@ def lib():
         L.jk_status_string.restype = ctypes.c_char_p
         L.jk_last_error.argtypes = []
         L.jk_last_error.restype = ctypes.c_char_p
+        L.jk_microbench_fma.argtypes = [ctypes.c_int, dp]
         _lib = L
     return _lib
 
@@ -215,6 +217,12 @@ class Plan:
         _check(lib().jk_build_times(self._h, ms, nl, 7), "jk_build_times")
         return {p: (ms[i], nl[i]) for i, p in enumerate(self.PHASES)}
 
+    def build_counts(self):
+        """(FP64 image quartets, FP32 image quartets) of the most recent build."""
+        c = (ctypes.c_longlong * 4)()
+        _check(lib().jk_build_counts(self._h, c, 4), "jk_build_counts")
+        return int(c[0]), int(c[1])
+
     def energy(self, D_ptr: int, J_ptr: int, K_ptr: int, stream: int = 0):
         ej, ek = ctypes.c_double(), ctypes.c_double()
         _check(lib().jk_energy(self._h, D_ptr, J_ptr or None, K_ptr or None, ctypes.byref(ej), ctypes.byref(ek),
@@ -263,6 +271,13 @@ def ewald_point_charges(lattice, q, xyz, omega, delta=0.0) -> float:
     _check(lib().jk_ewald_point_charges(ctypes.byref(cell), len(q), _dp(q), _dp(xyz), float(omega), float(delta),
                                         ctypes.byref(e)), "jk_ewald_point_charges")
     return e.value
+
+
+def microbench_fma(fp64: bool) -> float:
+    """FMA throughput of the current device in TFLOP/s (measurement utility)."""
+    t = ctypes.c_double()
+    _check(lib().jk_microbench_fma(1 if fp64 else 0, ctypes.byref(t)), "jk_microbench_fma")
+    return t.value
 
 
 class Server:

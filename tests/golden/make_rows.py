@@ -1,0 +1,38 @@
+"""Write oracle J/K rows for sampled shells of a full-size synthetic cell.
+
+Calls only the oracle (oracle/) and the seeded input generator
+(synthcells/).  The stored rows are the expected values of the full-size
+parity tests (sampled outputs the oracle can compute one by one).
+
+usage: python tests/golden/make_rows.py water [shell ...]
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import synthcells as sc  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+
+CELLS = {"water": lambda: sc.config(2), "diamond": lambda: sc.config(3)}
+
+
+def main():
+    name = sys.argv[1]
+    cell = CELLS[name]()
+    shells = [int(x) for x in sys.argv[2:]] or [0]
+    t = time.time()
+    D = O.density(cell)
+    J, K = O.jk_rows(cell, D, shells)
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "%s_rows_%s.npz" % (name, "_".join(map(str, shells))))
+    np.savez_compressed(out, shells=np.array(shells), rows=O.row_indices(cell, shells), J=J, K=K,
+                        seconds=time.time() - t, threads=O.num_threads())
+    print(out, "%.1f s" % (time.time() - t))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,80 @@
+"""Request server (continuous batching) through the C ABI: every result is
+the same alone and in the mix, admission respects the HBM budget, unknown
+tickets are reported."""
+import numpy as np
+import pytest
+
+import synthcells as sc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def jk():
+    from paper_2410_22278_gb300 import build, jk
+
+    build.build()
+    return jk
+
+
+def _cells():
+    return [sc.config(1), sc.small_random_cell(3, natom=2, lmax=2), sc.small_random_cell(4, natom=3, lmax=1)]
+
+
+def _density(cell, k):
+    rng = np.random.default_rng(100 + k)
+    X = rng.standard_normal((cell.nbf, cell.nbf))
+    return 0.05 * (X + X.T) + np.eye(cell.nbf)
+
+
+def test_results_alone_equal_results_in_the_mix(jk):
+    dev = torch.device("cuda:0")
+    cells = _cells()
+    plans = [jk.plan_from_cell(c) for c in cells]
+    alone = []
+    Ds = []
+    for k, (c, p) in enumerate(zip(cells, plans)):
+        D = torch.from_numpy(_density(c, k)).to(dev)
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        p.build(D.data_ptr(), J.data_ptr(), K.data_ptr(), 0)
+        torch.cuda.synchronize()
+        alone.append((J.cpu().numpy(), K.cpu().numpy()))
+        Ds.append(D)
+    srv = jk.Server(device=0, hbm_budget_bytes=8 << 30, max_slots=2)
+    outs, tickets = [], []
+    for rep in range(3):
+        for k, p in enumerate(plans):
+            J = torch.empty_like(Ds[k])
+            K = torch.empty_like(Ds[k])
+            outs.append((k, J, K))
+            tickets.append(srv.submit(p, Ds[k].data_ptr(), J.data_ptr(), K.data_ptr()))
+    lat = []
+    for t in tickets:
+        st, l = srv.wait(t, timeout_ms=60000)
+        assert st == 0
+        lat.append(l)
+    for k, J, K in outs:
+        assert np.abs(J.cpu().numpy() - alone[k][0]).max() < 1e-12
+        assert np.abs(K.cpu().numpy() - alone[k][1]).max() < 1e-12
+    assert all(l > 0 for l in lat)
+    with pytest.raises(jk.JkError) as e:
+        srv.wait(tickets[0], timeout_ms=10)
+    assert e.value.status == jk.JK_ERR_NOT_FOUND
+    srv.close()
+    for p in plans:
+        p.close()
+
+
+def test_budget_refusal(jk):
+    cell = sc.config(1)
+    p = jk.plan_from_cell(cell)
+    srv = jk.Server(device=0, hbm_budget_bytes=1024, max_slots=1)
+    D = torch.eye(cell.nbf, dtype=torch.float64, device="cuda:0")
+    J = torch.empty_like(D)
+    with pytest.raises(jk.JkError) as e:
+        srv.submit(p, D.data_ptr(), J.data_ptr(), 0)
+    assert e.value.status == jk.JK_ERR_OOM
+    srv.close()
+    p.close()
