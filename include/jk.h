@@ -158,7 +158,10 @@ int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
 
 /* Work counters of the most recent jk_build (waits for it to finish):
  * counts[0] unique image quartets evaluated in real space in FP64,
- * counts[1] those evaluated in FP32 (mixed precision only).  n <= 4. */
+ * counts[1] those evaluated in FP32 (mixed precision only), counts[2]
+ * quartets that the mixed policy wanted in FP64 but that overflowed the
+ * plan's FP64 list and were evaluated in FP32 (0 in a healthy build).
+ * n <= 4. */
 int jk_build_counts(jk_plan *plan, long long *counts, int n);
 
 /* Gamma overlap over the plan's pair list (Eq. pbc_overlap_formula),

@@ -18,6 +18,7 @@
 #include "kernels.cuh"
 #include "launch.h"
 #include "plan.h"
+#include "real_units.h"
 
 namespace jk {
 
@@ -26,6 +27,11 @@ __global__ void k_scale(int n, const double *__restrict__ f, const double *__res
     const size_t n2 = (size_t)n * n;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x)
         B[i] = f[i / n] * f[i % n] * A[i];
+}
+
+__global__ void k_to_float(size_t n, const double *__restrict__ a, float *__restrict__ b)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
 }
 
 __global__ void k_dmax(PlanDev pl, const double *__restrict__ Dp, double *__restrict__ dmax)
@@ -108,19 +114,6 @@ void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv,
     }
 }
 
-static void launch_real(int cb, int ck, const RealLaunch &a)
-{
-    switch (cb) {
-    case 0: launch_real_c0(ck, a); break;
-    case 1: launch_real_c1(ck, a); break;
-    case 2: launch_real_c2(ck, a); break;
-    case 3: launch_real_c3(ck, a); break;
-    case 4: launch_real_c4(ck, a); break;
-    case 5: launch_real_c5(ck, a); break;
-    default: break;
-    }
-}
-
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
 static int cuda_check(const char *what)
@@ -194,6 +187,8 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     if (mixed) {
         const long long ns2 = (long long)P->nshell * P->nshell;
         k_dmax<<<(unsigned)((ns2 + 255) / 256), 256, 0, st>>>(pl, w.Dp, w.dmax);
+        k_to_float<<<grid_for(n2), 256, 0, st>>>(n2, w.Dp, w.Dpf);
+        k_to_float<<<grid_for((size_t)ns2), 256, 0, st>>>((size_t)ns2, w.dmax, w.dmaxf);
     }
     cudaMemsetAsync(w.X, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.Y, 0, n2 * sizeof(double), st);
@@ -201,9 +196,10 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     cudaMemsetAsync(w.KLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), st);
     cudaMemsetAsync(w.cnt, 0, 4 * sizeof(unsigned long long), st);
+    if (w.nbig) cudaMemsetAsync(w.nbig, 0, 2 * sizeof(unsigned), st);
     int rc;
     if ((rc = cuda_check("prologue"))) return rc;
-    tm.stop(0, ev, mixed ? 2 : 1);
+    tm.stop(0, ev, mixed ? 4 : 1);
 
     // ---- real space
     ev = tm.start(1);
@@ -223,6 +219,8 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             a.tau = P->mixed_tau;
             a.Dp = w.Dp;
             a.dmax = w.dmax;
+            a.Dpf = w.Dpf;
+            a.dmaxf = w.dmaxf;
             a.X = w.X;
             a.Y = w.Y;
             a.st = st;
@@ -233,13 +231,19 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
                 launch_real(cb, ck, a);
                 nreal += 1;
             } else {
-                a.mode = 1;
-                a.fp32 = false;
-                a.cnt = w.cnt;
-                launch_real(cb, ck, a);
+                // FP32 pass over every quartet, collecting the large ones ...
+                cudaMemsetAsync(w.nbig, 0, sizeof(unsigned), st);
                 a.mode = 2;
                 a.fp32 = true;
                 a.cnt = w.cnt + 1;
+                a.big = w.big;
+                a.nbig = w.nbig;
+                a.ovf = w.nbig + 1;
+                a.cap = w.cap;
+                launch_real(cb, ck, a);
+                // ... then FP64 over the compact list
+                a.list_pass = true;
+                a.cnt64 = w.cnt;
                 launch_real(cb, ck, a);
                 nreal += 2;
             }
@@ -250,6 +254,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
 
     // ---- reciprocal space
     const int ng = (int)(P->gvec.size() / 4);
+    if (mixed && K && (rc = ozaki_slice_density(P, st))) return rc;
     for (int g0 = 0; g0 < ng; g0 += w.gc) {
         const int gcur = std::min(w.gc, ng - g0);
         ev = tm.start(2);
@@ -270,15 +275,17 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
         }
         if (K) {
             ev = tm.start(4);
-            // FP64 path: native DGEMM; mixed path: DGEMM with cuBLAS's fixed-point
-            // FP64 emulation on the tensor cores (FP64-accurate products)
-            BLAS_OK(cublasSetMathMode(P->blas, mixed ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH : CUBLAS_DEFAULT_MATH));
-            if (mixed) BLAS_OK(cublasSetEmulationStrategy(P->blas, CUBLAS_EMULATION_STRATEGY_EAGER));
-            BLAS_OK(cublasDgemmStridedBatched(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, w.Dp, n, 0, w.M, n, (long long)n2,
-                                              &zero, w.Z, m2 * n, n, m2));
-            BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, m2 * n, &one, w.M, n, w.Z, m2 * n, &one, w.KLR, n));
-            BLAS_OK(cublasSetMathMode(P->blas, CUBLAS_DEFAULT_MATH));
-            tm.stop(4, ev, 2);
+            if (mixed) {
+                // split-precision BF16 tensor-core GEMMs (about 42 significant bits)
+                if ((rc = ozaki_exchange_chunk(P, m2, w.Ds, w.Dex, st))) return rc;
+                tm.stop(4, ev, 4);
+            } else {
+                // the plain FP64 form: K_LR += [M_1 .. M_2g] [Z_1; ..; Z_2g], Z_b = D' M_b (native DGEMM)
+                BLAS_OK(cublasDgemmStridedBatched(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, w.Dp, n, 0, w.M, n, (long long)n2,
+                                                  &zero, w.Z, m2 * n, n, m2));
+                BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, m2 * n, &one, w.M, n, w.Z, m2 * n, &one, w.KLR, n));
+                tm.stop(4, ev, 2);
+            }
         }
     }
     ev = tm.start(5);
@@ -300,9 +307,13 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
 int build_counts(Plan *P, long long *counts, int n)
 {
     unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned hb[2] = {0, 0};
     if (P->timer.next > 0 && cudaEventSynchronize(P->timer.pool[P->timer.next - 1]) != cudaSuccess)
         return fail(JK_ERR_CUDA, "build did not finish");
     if (cudaMemcpy(h, P->ws.cnt, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(JK_ERR_CUDA, "count copy failed");
+    if (P->ws.nbig && cudaMemcpy(hb, P->ws.nbig, sizeof hb, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(JK_ERR_CUDA, "count copy failed");
+    h[2] = hb[1];
     for (int i = 0; i < n && i < 4; ++i) counts[i] = (long long)h[i];
     return JK_OK;
 }

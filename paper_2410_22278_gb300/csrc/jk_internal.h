@@ -82,7 +82,9 @@ struct PlanDev {
     const double *compf;         // Cartesian component factor of each AO
     double L[9];                 // lattice rows a, b, c
     double Finv[9];              // fractional coordinates f = Finv * r
+    float Lf[9], Finvf[9];       // the same in single precision (no conversions in FP32 kernels)
     double omega, inv_omega2;
+    float inv_omega2f;
     double ewald_R;              // delta_Ewald-R as given
     float log_ewald_R;           // ln of the per-term threshold used inside the real-space sums
     double volume;

@@ -34,6 +34,38 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) { return warp_sum(v); }
+
+// Running sum over the ket loop: plain in double; in float a compensated
+// (two-sum) pair, so the per-lane Coulomb partial keeps ~48 bits.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float t = hi + v;
+        const float bp = t - hi;
+        lo += (hi - (t - bp)) + (v - bp);
+        hi = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Attenuated seeds s_m = (-2 alpha)^m F_m(alpha X^2) - c_w (-2 alpha_w)^m F_m(alpha_w X^2)
 // = (-2 alpha)^m G_m(alpha X^2, c_w)  (see boys_attenuated).
 template <int L>
@@ -102,6 +134,8 @@ __device__ __forceinline__ void load_pair(const PlanDev &, int, const PpiF &f, P
     o.ip = f.pad;
     o.K = f.K;
 }
+__device__ __forceinline__ double latc(const double *d, const float *, int k, double) { return d[k]; }
+__device__ __forceinline__ float latc(const double *, const float *f, int k, float) { return f[k]; }
 __device__ __forceinline__ double lat_at(const PlanDev &pl, int k, double) { return pl.r1[k]; }
 __device__ __forceinline__ float lat_at(const PlanDev &pl, int k, float) { return pl.r1f[k]; }
 
@@ -116,7 +150,10 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int L = LA + LB + LC + LD, LAB = LA + LB, LCD = LC + LD;
     constexpr int NTA = LAB + 1, NTC = LCD + 1, D = L + 1;
-    const float iw2 = (float)pl.inv_omega2;
+    // classes of total momentum >= 6 (d shells) keep their component loops
+    // rolled: full unrolling there only bloats code and compile time
+    constexpr int UNR = L >= 6 ? 1 : 64;
+    const float iw2 = pl.inv_omega2f;
     for (int i = 0; i < sb.npp; ++i) {
         const PpiF xf = pl.ppf[sb.pp0 + i];
         PairT<T> x;
@@ -137,6 +174,8 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             float r = sqrtf(lg / awf);
             r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
             r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+            // the Gaussian bound is derived for s functions; widen for L > 0
+            r += L > 0 ? 0.5f + 0.25f * L : 0.0f;
             const float r2 = r * r;
             PairT<T> y;
             load_pair(pl, sk.pp0 + j, yf, y);
@@ -146,9 +185,11 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
                 T f[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    f[a] = rint(T(pl.Finv[3 * a]) * X0[0] + T(pl.Finv[3 * a + 1]) * X0[1] + T(pl.Finv[3 * a + 2]) * X0[2]);
+                    f[a] = rint(latc(pl.Finv, pl.Finvf, 3 * a, T(0)) * X0[0] + latc(pl.Finv, pl.Finvf, 3 * a + 1, T(0)) * X0[1] +
+                                latc(pl.Finv, pl.Finvf, 3 * a + 2, T(0)) * X0[2]);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) X0[a] -= f[0] * T(pl.L[a]) + f[1] * T(pl.L[3 + a]) + f[2] * T(pl.L[6 + a]);
+                for (int a = 0; a < 3; ++a)
+                    X0[a] -= f[0] * latc(pl.L, pl.Lf, a, T(0)) + f[1] * latc(pl.L, pl.Lf, 3 + a, T(0)) + f[2] * latc(pl.L, pl.Lf, 6 + a, T(0));
             }
             const float x0n = sqrtf((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
             T Rs[D * D * D];
@@ -156,7 +197,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             for (int k = 0; k < D * D * D; ++k) Rs[k] = T(0);
             bool any = false;
             const T ip = x.ip, iq = y.ip;
-            const T aw = T(1) / (ip + iq + T(pl.inv_omega2));
+            const T aw = T(1) / (ip + iq + latc(&pl.inv_omega2, &pl.inv_omega2f, 0, T(0)));
             const T alpha = T(1) / (ip + iq);
             const T cw = sqrt(aw * (ip + iq));
             for (int c = 0; c < pl.nr1; ++c) {
@@ -183,9 +224,9 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
 #pragma unroll
             for (int k = 0; k < 3; ++k) herm_E<LC, LD, T>(y.PA[k], y.PB[k], oo2q, Ec[k]);
             const T tp = T(kTwoPi52) * x.K * y.K * ip * iq / sqrt(x.p + y.p);
-            #pragma unroll
+#pragma unroll UNR
             for (int c = 0; c < NC; ++c)
-#pragma unroll
+#pragma unroll UNR
                 for (int d = 0; d < ND; ++d) {
                     const int cx = cexp(LC, c, 0), cy = cexp(LC, c, 1), cz = cexp(LC, c, 2);
                     const int dx = cexp(LD, d, 0), dy = cexp(LD, d, 1), dz = cexp(LD, d, 2);
@@ -213,9 +254,9 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
                                         }
                                 W[(tx * NTA + ty) * NTA + tz] = acc;
                             }
-#pragma unroll
+#pragma unroll UNR
                     for (int a = 0; a < NA; ++a)
-#pragma unroll
+#pragma unroll UNR
                         for (int b = 0; b < NB; ++b) {
                             const int ax = cexp(LA, a, 0), ay = cexp(LA, a, 1), az = cexp(LA, a, 2);
                             const int bx = cexp(LB, b, 0), by = cexp(LB, b, 1), bz = cexp(LB, b, 2);
@@ -245,11 +286,11 @@ __device__ __forceinline__ float quartet_estimate(const PlanDev &pl, const SpiRe
     float X[3] = {sb.Pc[0] - sk.Pc[0], sb.Pc[1] - sk.Pc[1], sb.Pc[2] - sk.Pc[2]};
     float f[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) f[a] = rintf((float)pl.Finv[3 * a] * X[0] + (float)pl.Finv[3 * a + 1] * X[1] + (float)pl.Finv[3 * a + 2] * X[2]);
+    for (int a = 0; a < 3; ++a) f[a] = rintf(pl.Finvf[3 * a] * X[0] + pl.Finvf[3 * a + 1] * X[1] + pl.Finvf[3 * a + 2] * X[2]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) X[a] -= f[0] * (float)pl.L[a] + f[1] * (float)pl.L[3 + a] + f[2] * (float)pl.L[6 + a];
+    for (int a = 0; a < 3; ++a) X[a] -= f[0] * pl.Lf[a] + f[1] * pl.Lf[3 + a] + f[2] * pl.Lf[6 + a];
     const float d = fmaxf(0.0f, sqrtf(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
-    const float d2 = d * d, iw2 = (float)pl.inv_omega2;
+    const float d2 = d * d, iw2 = pl.inv_omega2f;
     float est = 0.0f;
     for (int i = 0; i < sb.npp; ++i) {
         const PpiF x = pl.ppf[sb.pp0 + i];
@@ -263,16 +304,21 @@ __device__ __forceinline__ float quartet_estimate(const PlanDev &pl, const SpiRe
     return est;
 }
 
-// mode: 0 every quartet; 1 only quartets whose density-weighted size
-// estimate is >= tau; 2 only those below tau.  cnt[0] counts the image
-// quartets evaluated, cnt[1] the primitive quartets inside the sphere.
+// mode 0: every quartet in this kernel's precision.  mode 2 (mixed
+// precision, T = float): quartets whose density-weighted size estimate is
+// >= tau are appended to the compact list `big` (processed afterwards in
+// FP64 by k_real_list) instead of being evaluated here; if the list is full
+// the quartet is evaluated here and counted in ovf.  *cnt counts the image
+// quartets this launch evaluated.
 template <int LA, int LB, int LC, int LD, typename T>
 __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
-                                                        double tau, const double *__restrict__ Dp, const double *__restrict__ dmax,
+                                                        double tau, const T *__restrict__ Dp, const T *__restrict__ dmax,
                                                         double *__restrict__ X, double *__restrict__ Y,
-                                                        unsigned long long *__restrict__ cnt)
+                                                        unsigned long long *__restrict__ cnt, int2 *__restrict__ big,
+                                                        unsigned *__restrict__ nbig, unsigned cap, unsigned *__restrict__ ovf)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int DUNR = LA + LB + LC + LD >= 6 ? 1 : 64;
     const int tile0 = b0 + blockIdx.x * kRealThreads;
     const int bra = tile0 + threadIdx.x;
     int kbeg = k0 + blockIdx.y * kchunk;
@@ -283,111 +329,218 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
     const SpiRec sb = pl.spi[act ? bra : b0];
     const int n = pl.nbf, nsh = pl.nshell;
     const int aoI = pl.shells[sb.I].ao, aoJ = pl.shells[sb.J].ao;
-    double Dij[NA * NB], jb[NA * NB];
+    T Dij[NA * NB];
+    Acc<T> jb[NA * NB];
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            Dij[a * NB + b] = __ldg(Dp + (size_t)(aoI + a) * n + aoJ + b);
-            jb[a * NB + b] = 0.0;
-        }
-    const double dIJ = mode ? dmax[sb.I * nsh + sb.J] : 0.0;
+        for (int b = 0; b < NB; ++b) Dij[a * NB + b] = __ldg(Dp + (size_t)(aoI + a) * n + aoJ + b);
+    const T dIJ = mode ? dmax[sb.I * nsh + sb.J] : T(0);
+    const float tauf = (float)tau;
     unsigned nq = 0;
     for (int kt = kbeg; kt < kend; ++kt) {
         const SpiRec sk = pl.spi[kt];
         bool valid = act && (!same || kt >= bra);
         if (valid && mode) {
-            double dm = fmax(fmax(dIJ, dmax[sk.I * nsh + sk.J]), fmax(dmax[sb.J * nsh + sk.I], dmax[sb.I * nsh + sk.I]));
-            dm = fmax(dm, fmax(dmax[sb.J * nsh + sk.J], dmax[sb.I * nsh + sk.J]));
-            const double est = (double)quartet_estimate(pl, sb, sk) * dm;
-            valid = (mode == 1) ? (est >= tau) : (est < tau);
+            float dm = fmaxf(fmaxf((float)dIJ, (float)dmax[sk.I * nsh + sk.J]), fmaxf((float)dmax[sb.J * nsh + sk.I], (float)dmax[sb.I * nsh + sk.I]));
+            dm = fmaxf(dm, fmaxf((float)dmax[sb.J * nsh + sk.J], (float)dmax[sb.I * nsh + sk.J]));
+            const float est = quartet_estimate(pl, sb, sk) * dm;
+            if (est >= tauf) {
+                const unsigned slot = atomicAdd(nbig, 1u);
+                if (slot < cap) {
+                    big[slot] = make_int2(bra, kt);
+                    valid = false;
+                } else {
+                    atomicAdd(ovf, 1u);
+                }
+            }
         }
         T V[NA * NB * NC * ND];
 #pragma unroll
         for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = T(0);
         if (valid) quartet_block<LA, LB, LC, LD, T>(pl, sb, sk, V);
         nq += valid;
-        const double w = valid ? double(sb.w) * double(sk.w) * ((same && kt == bra) ? 0.5 : 1.0) : 0.0;
+        // orbit weight, exact in either precision
+        const T w = valid ? T(sb.w) * T(sk.w) * ((same && kt == bra) ? T(0.5) : T(1)) : T(0);
         const int aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
-        // Coulomb, bra side: X_ij += 2w sum_kl V D_kl (held in registers over the ket loop)
-        double Dkl[NC * ND];
+        // Coulomb, bra side: X_ij += 2w sum_kl V D_kl (held over the ket loop)
+        T Dkl[NC * ND];
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int d = 0; d < ND; ++d) Dkl[c * ND + d] = __ldg(Dp + (size_t)(aoK + c) * n + aoL + d);
 #pragma unroll
         for (int ab = 0; ab < NA * NB; ++ab) {
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
-            for (int cd = 0; cd < NC * ND; ++cd) s += double(V[ab * NC * ND + cd]) * Dkl[cd];
-            jb[ab] += 2.0 * w * s;
+            for (int cd = 0; cd < NC * ND; ++cd) s += V[ab * NC * ND + cd] * Dkl[cd];
+            jb[ab].add(T(2) * w * s);
         }
         // Coulomb, ket side: X_kl += 2w sum_ij V D_ij, summed over the warp's bras
 #pragma unroll
         for (int cd = 0; cd < NC * ND; ++cd) {
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
-            for (int ab = 0; ab < NA * NB; ++ab) s += double(V[ab * NC * ND + cd]) * Dij[ab];
-            s = warp_sum(2.0 * w * s);
-            if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, s);
+            for (int ab = 0; ab < NA * NB; ++ab) s += V[ab * NC * ND + cd] * Dij[ab];
+            s = warp_sum_t(T(2) * w * s);
+            if ((threadIdx.x & 31) == 0 && s != T(0)) atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, (double)s);
         }
         // exchange: the four index assignments of the orbit (the other four are transposes)
         if (valid) {
-#pragma unroll
+#pragma unroll DUNR
             for (int a = 0; a < NA; ++a)
-#pragma unroll
+#pragma unroll DUNR
                 for (int d = 0; d < ND; ++d) {  // K_il += w V_ijkl D_jk
-                    double s = 0.0;
+                    T s = T(0);
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) s += double(V[((a * NB + b) * NC + c) * ND + d]) * __ldg(Dp + (size_t)(aoJ + b) * n + aoK + c);
-                    atomicAdd(Y + (size_t)(aoI + a) * n + aoL + d, w * s);
+                        for (int c = 0; c < NC; ++c) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoJ + b) * n + aoK + c);
+                    atomicAdd(Y + (size_t)(aoI + a) * n + aoL + d, (double)(w * s));
                 }
-#pragma unroll
+#pragma unroll DUNR
             for (int b = 0; b < NB; ++b)
-#pragma unroll
+#pragma unroll DUNR
                 for (int d = 0; d < ND; ++d) {  // K_jl += w V_ijkl D_ik
-                    double s = 0.0;
+                    T s = T(0);
 #pragma unroll
                     for (int a = 0; a < NA; ++a)
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) s += double(V[((a * NB + b) * NC + c) * ND + d]) * __ldg(Dp + (size_t)(aoI + a) * n + aoK + c);
-                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoL + d, w * s);
+                        for (int c = 0; c < NC; ++c) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoI + a) * n + aoK + c);
+                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoL + d, (double)(w * s));
                 }
-#pragma unroll
+#pragma unroll DUNR
             for (int a = 0; a < NA; ++a)
-#pragma unroll
+#pragma unroll DUNR
                 for (int c = 0; c < NC; ++c) {  // K_ik += w V_ijkl D_jl
-                    double s = 0.0;
+                    T s = T(0);
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) s += double(V[((a * NB + b) * NC + c) * ND + d]) * __ldg(Dp + (size_t)(aoJ + b) * n + aoL + d);
-                    atomicAdd(Y + (size_t)(aoI + a) * n + aoK + c, w * s);
+                        for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoJ + b) * n + aoL + d);
+                    atomicAdd(Y + (size_t)(aoI + a) * n + aoK + c, (double)(w * s));
                 }
-#pragma unroll
+#pragma unroll DUNR
             for (int b = 0; b < NB; ++b)
-#pragma unroll
+#pragma unroll DUNR
                 for (int c = 0; c < NC; ++c) {  // K_jk += w V_ijkl D_il
-                    double s = 0.0;
+                    T s = T(0);
 #pragma unroll
                     for (int a = 0; a < NA; ++a)
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) s += double(V[((a * NB + b) * NC + c) * ND + d]) * __ldg(Dp + (size_t)(aoI + a) * n + aoL + d);
-                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoK + c, w * s);
+                        for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoI + a) * n + aoL + d);
+                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoK + c, (double)(w * s));
                 }
         }
     }
     if (act) {
-#pragma unroll
+#pragma unroll DUNR
         for (int a = 0; a < NA; ++a)
-#pragma unroll
-            for (int b = 0; b < NB; ++b)
-                if (jb[a * NB + b] != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, jb[a * NB + b]);
+#pragma unroll DUNR
+            for (int b = 0; b < NB; ++b) {
+                const double v = jb[a * NB + b].value();
+                if (v != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, v);
+            }
     }
     // warp-aggregated count of the image quartets this launch evaluated
     unsigned tot = nq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);
+}
+
+// FP64 pass over the compact list of large quartets collected by the
+// mixed-precision kernel of the same class pair (grid-stride; each entry is
+// one unique pair of images, digested with the same orbit weights).
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const int2 *__restrict__ big, const unsigned *__restrict__ nbig,
+                                                             unsigned cap, int same, const double *__restrict__ Dp, double *__restrict__ X,
+                                                             double *__restrict__ Y, unsigned long long *__restrict__ cnt)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int DUNR = LA + LB + LC + LD >= 6 ? 1 : 64;
+    const unsigned total = min(*nbig, cap);
+    const int n = pl.nbf;
+    unsigned done = 0;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int2 q = big[e];
+        const SpiRec sb = pl.spi[q.x], sk = pl.spi[q.y];
+        double V[NA * NB * NC * ND];
+#pragma unroll
+        for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = 0.0;
+        quartet_block<LA, LB, LC, LD, double>(pl, sb, sk, V);
+        ++done;
+        const double w = double(sb.w) * double(sk.w) * ((same && q.x == q.y) ? 0.5 : 1.0);
+        const int aoI = pl.shells[sb.I].ao, aoJ = pl.shells[sb.J].ao, aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
+        auto Dd = [&](int r, int c) { return __ldg(Dp + (size_t)r * n + c); };
+#pragma unroll DUNR
+        for (int a = 0; a < NA; ++a)
+#pragma unroll DUNR
+            for (int b = 0; b < NB; ++b) {
+                double s = 0;
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoK + c, aoL + d);
+                atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, 2.0 * w * s);
+            }
+#pragma unroll DUNR
+        for (int c = 0; c < NC; ++c)
+#pragma unroll DUNR
+            for (int d = 0; d < ND; ++d) {
+                double s = 0;
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoI + a, aoJ + b);
+                atomicAdd(X + (size_t)(aoK + c) * n + aoL + d, 2.0 * w * s);
+            }
+#pragma unroll DUNR
+        for (int a = 0; a < NA; ++a)
+#pragma unroll DUNR
+            for (int d = 0; d < ND; ++d) {
+                double s = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoJ + b, aoK + c);
+                atomicAdd(Y + (size_t)(aoI + a) * n + aoL + d, w * s);
+            }
+#pragma unroll DUNR
+        for (int b = 0; b < NB; ++b)
+#pragma unroll DUNR
+            for (int d = 0; d < ND; ++d) {
+                double s = 0;
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoI + a, aoK + c);
+                atomicAdd(Y + (size_t)(aoJ + b) * n + aoL + d, w * s);
+            }
+#pragma unroll DUNR
+        for (int a = 0; a < NA; ++a)
+#pragma unroll DUNR
+            for (int c = 0; c < NC; ++c) {
+                double s = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoJ + b, aoL + d);
+                atomicAdd(Y + (size_t)(aoI + a) * n + aoK + c, w * s);
+            }
+#pragma unroll DUNR
+        for (int b = 0; b < NB; ++b)
+#pragma unroll DUNR
+            for (int c = 0; c < NC; ++c) {
+                double s = 0;
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoI + a, aoL + d);
+                atomicAdd(Y + (size_t)(aoJ + b) * n + aoK + c, w * s);
+            }
+    }
+    unsigned tot = done;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);

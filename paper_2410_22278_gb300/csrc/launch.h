@@ -12,19 +12,17 @@ struct RealLaunch {
     int b0, b1, k0, k1, same, kchunk, mode;
     double tau;
     bool fp32;
-    const double *Dp, *dmax;
+    const double *Dp, *dmax;      // FP64 kernels
+    const float *Dpf, *dmaxf;     // FP32 kernels
     double *X, *Y;
     unsigned long long *cnt;
+    int2 *big;           // compact list of large quartets (mixed precision)
+    unsigned *nbig, *ovf;
+    unsigned cap;
+    bool list_pass;      // launch k_real_list over the list instead of the tile kernel
+    unsigned long long *cnt64;
     cudaStream_t st;
 };
-
-// one function per bra class cb (0..5); ck >= cb selects the ket class
-void launch_real_c0(int ck, const RealLaunch &a);
-void launch_real_c1(int ck, const RealLaunch &a);
-void launch_real_c2(int ck, const RealLaunch &a);
-void launch_real_c3(int ck, const RealLaunch &a);
-void launch_real_c4(int ck, const RealLaunch &a);
-void launch_real_c5(int ck, const RealLaunch &a);
 
 void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, double *M, cudaStream_t st);
 

@@ -190,6 +190,7 @@ static double realspace_r2(double p, double q, double KK, double omega, double d
     if (lg <= 0) return -1.0;
     double r = std::sqrt(lg / aw);
     for (int it = 0; it < 3; ++it) r = std::sqrt((lg + L * std::log(1.0 + 2.0 * aw * r)) / aw);
+    r += L > 0 ? 0.5 + 0.25 * L : 0.0;
     return r * r;
 }
 
@@ -217,12 +218,18 @@ PlanDev Plan::dev() const
     d.compf = d_compf;
     memcpy(d.L, L, sizeof L);
     memcpy(d.Finv, Finv, sizeof Finv);
+    for (int i = 0; i < 9; ++i) {
+        d.Lf[i] = (float)L[i];
+        d.Finvf[i] = (float)Finv[i];
+    }
     d.omega = omega;
     d.inv_omega2 = 1.0 / (omega * omega);
+    d.inv_omega2f = (float)d.inv_omega2;
     d.ewald_R = cut.ewald_R;
     // Eq. pbc_eri_real_cutoff_definition bounds one term; a matrix element
-    // sums 1e2-1e4 such terms, so the sphere is drawn at delta_Ewald-R / 100.
-    d.log_ewald_R = (float)std::log(cut.ewald_R * 1e-2);
+    // sums many such terms, so the sphere is drawn at delta_Ewald-R / 10
+    // (plus an angular-momentum margin in the kernels).
+    d.log_ewald_R = (float)std::log(cut.ewald_R * 1e-1);
     d.volume = volume;
     return d;
 }
@@ -243,9 +250,16 @@ static int alloc_ws(Plan *P)
     Workspace &w = P->ws;
     size_t n2 = (size_t)P->nbf * P->nbf;
     int ng = (int)(P->gvec.size() / 4);
-    // structure-factor chunk: M and Z, each 2*gc*n^2 doubles, kept within ~4 GB together
+    const bool mixed = P->precision == JK_MIXED;
+    if (mixed) {
+        w.oz_slices = 6;  // 7-bit slices: about 42 significant bits per operand
+        w.npad = (P->nbf + 127) / 128 * 128;
+    }
+    // per G: the structure-factor slab M and its GEMM partner Z (2 n^2 doubles
+    // each) plus, in mixed precision, the BF16 slices of both; ~4 GB in total
+    const double per_g = 32.0 * (double)n2 + (mixed ? 4.0 * 2.0 * w.oz_slices * (double)w.npad * w.npad : 0.0);
     double budget = 4.0e9;
-    long long gc = (long long)(budget / (32.0 * (double)n2));
+    long long gc = (long long)(budget / per_g);
     gc = std::max<long long>(1, std::min<long long>(gc, std::max(ng, 1)));
     gc = std::min<long long>(gc, 4096);
     w.gc = (int)gc;
@@ -257,12 +271,37 @@ static int alloc_ws(Plan *P)
     };
     bool ok = al(&w.Dp, n2) && al(&w.X, n2) && al(&w.Y, n2) && al(&w.JLR, n2) && al(&w.KLR, n2) && al(&w.T1, n2) &&
               al(&w.T2, n2) && al(&w.M, 2 * (size_t)gc * n2) && al(&w.Z, 2 * (size_t)gc * n2) && al(&w.rho, 2 * (size_t)gc) &&
-              al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16);
+              al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16) && (!mixed || al((double **)&w.Dpf, (n2 + 1) / 2)) &&
+              (!mixed || al((double **)&w.dmaxf, ((size_t)P->nshell * P->nshell + 1) / 2));
     if (!ok) return fail(JK_ERR_OOM, "cudaMalloc failed for build workspace");
+    if (mixed) {
+        const size_t sl = (size_t)w.oz_slices * w.npad * w.npad;
+        auto alb = [&](__nv_bfloat16 **ptr, size_t count) -> bool {
+            if (cudaMalloc((void **)ptr, count * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
+            bytes += count * sizeof(__nv_bfloat16);
+            return true;
+        };
+        auto ali = [&](int **ptr, size_t count) -> bool {
+            if (cudaMalloc((void **)ptr, count * sizeof(int)) != cudaSuccess) return false;
+            bytes += count * sizeof(int);
+            return true;
+        };
+        if (!alb(&w.Ms, 2 * (size_t)gc * sl) || !alb(&w.Zs, 2 * (size_t)gc * sl) || !alb(&w.Ds, sl) ||
+            !ali(&w.Mex, 2 * (size_t)gc * w.npad) || !ali(&w.Zex, 2 * (size_t)gc * w.npad) || !ali(&w.Dex, w.npad))
+            return fail(JK_ERR_OOM, "cudaMalloc failed for tensor-core exchange workspace");
+    }
     if (cudaMalloc((void **)&w.err, sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
     if (cudaMalloc((void **)&w.cnt, 4 * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
+    if (P->precision == JK_MIXED) {
+        // the FP64 share is a small fraction; the list holds up to 2% of all image quartets (at most 64 Mi entries)
+        const long long want = std::min<long long>(std::max<long long>(P->n_quartets / 50, 1 << 20), 64ll << 20);
+        w.cap = (unsigned)want;
+        if (cudaMalloc((void **)&w.big, sizeof(int2) * w.cap) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed for quartet list");
+        if (cudaMalloc((void **)&w.nbig, 2 * sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
+        bytes += sizeof(int2) * w.cap + 2 * sizeof(unsigned);
+    }
     cudaMemset(w.err, 0, sizeof(unsigned));
-    w.bytes = bytes + sizeof(unsigned);
+    w.bytes = bytes + sizeof(unsigned) + 4 * sizeof(unsigned long long);
     return JK_OK;
 }
 
@@ -313,7 +352,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     if (!(c.pair_cs > 0)) c.pair_cs = 1e-14;
     if (!(c.ewald_R > 0)) c.ewald_R = 1e-14;
     if (!(c.ewald_K > 0)) c.ewald_K = 1e-14;
-    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-7;
+    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-5;  // the paper's switch-over value (Section 3.5)
     P->cut = c;
 
     // ---- shells, normalised coefficients, component factors
@@ -444,9 +483,12 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     std::vector<int> order(spis.size());
     std::iota(order.begin(), order.end(), 0);
     auto cls_of = [&](const SpiRec &s) { return pair_class(P->shells[s.I].l, P->shells[s.J].l); };
+    // class, then primitive-pair count (lanes of a warp do similar work),
+    // then descending Schwarz estimate (Section 3.1's prefactor order)
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         int ca = cls_of(spis[a]), cb = cls_of(spis[b]);
         if (ca != cb) return ca < cb;
+        if (spis[a].npp != spis[b].npp) return spis[a].npp > spis[b].npp;
         return spis[a].Q > spis[b].Q;
     });
     for (int idx : order) {
@@ -524,7 +566,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
         double rmax = 0;
         for (auto &u : kmax)
             for (auto &v : kmax) {
-                double r2 = realspace_r2(u.first, v.first, u.second * v.second, P->omega, c.ewald_R * 1e-2, 2 * lpmax);
+                double r2 = realspace_r2(u.first, v.first, u.second * v.second, P->omega, c.ewald_R * 1e-1, 2 * lpmax);
                 if (r2 > 0) rmax = std::max(rmax, std::sqrt(r2));
             }
         P->r1_max = rmax;
@@ -684,7 +726,8 @@ void destroy_plan(Plan *P)
     cudaSetDevice(P->device);
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
                     P->d_g0, P->d_compf, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
-                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt};
+                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
+                    P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P->blas) cublasDestroy(P->blas);

@@ -1,6 +1,7 @@
 // Host-side plan: built once per geometry (Section 3.1), then immutable.
 #pragma once
 #include <cublas_v2.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -32,11 +33,20 @@ struct Workspace {
     double *Z = nullptr;      // D * M chunk, stacked
     double *rho = nullptr;    // [2*gc] density structure factors
     double *dmax = nullptr;   // [nshell*nshell] max |D'| per shell block
+    float *Dpf = nullptr;     // single-precision copies for the FP32 kernels (mixed precision)
+    float *dmaxf = nullptr;
     double *scal = nullptr;   // small scalars (traces, energies)
     unsigned *err = nullptr;  // device check word
     unsigned long long *cnt = nullptr;  // [0] FP64 image quartets, [1] FP32 image quartets
+    int2 *big = nullptr;                // compact list of quartets sent to FP64 (mixed precision)
+    unsigned *nbig = nullptr;           // [0] list length, [1] overflow count (accumulated over a build)
+    unsigned cap = 0;
     int gc = 0;               // G vectors per chunk
     size_t bytes = 0;
+    // split-precision tensor-core exchange (mixed precision)
+    int npad = 0, oz_slices = 0;
+    __nv_bfloat16 *Ms = nullptr, *Zs = nullptr, *Ds = nullptr;
+    int *Mex = nullptr, *Zex = nullptr, *Dex = nullptr;
 };
 
 // CUDA events bracketing the phases of one build (see jk_build_times)
@@ -104,6 +114,8 @@ int run_build(Plan *p, const double *D, double *J, double *K, cudaStream_t st);
 int compute_overlap_raw(Plan *p, cudaStream_t st);
 int build_times(Plan *p, double *ms, int *launches, int n);
 int build_counts(Plan *p, long long *counts, int n);
+int ozaki_exchange_chunk(Plan *P, int m2, const __nv_bfloat16 *Ds, const int *Dex, cudaStream_t st);
+int ozaki_slice_density(Plan *P, cudaStream_t st);
 
 // host helpers shared by plan.cu and api.cu
 void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out);
