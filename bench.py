@@ -94,61 +94,125 @@ def make_workload(name="water64"):
 
 
 # ---------------------------------------------------------------------------------------------
+def oracle_sample(cell, D, n_bra=40, n_g=2):
+    """One bounded oracle sample: n_bra strided bra local pairs against every
+    ket local pair (real space) and n_g reciprocal vectors (pair transforms,
+    Coulomb and one exchange row), extrapolated to a full build."""
+    from oracle import oracle as O
+
+    nlp = O.pair_counts(cell)[2]
+    full_s, det = O.jk_sample_seconds(cell, D, max(1, nlp // n_bra), n_g)
+    return full_s, det
+
+
 def run_reference(args):
-    """The FP64 CPU oracle on the host cores, each step a bounded sample:
-    the J and K rows of one shell of the same water box, extrapolated to a
-    full build by the number of shells."""
+    """The FP64 CPU oracle on the host cores (the reference arm of this
+    build), each step a bounded sample of the same water-box build,
+    extrapolated to builds/s."""
     from oracle import oracle as O
 
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cell = make_workload()
+    cell = make_workload(args.workload)
     D = O.density(cell)
-    nsh = len(cell.shells)
-    # sample shells with one, three and six primitives so the mean is representative
-    sample_shells = [2, 11, 4, 20, 6, 24]
-    times = []
+    fulls, samples = [], []
     for i in range(args.warmup + args.steps):
-        sh = sample_shells[i % len(sample_shells)]
         t = time.perf_counter()
-        O.jk_rows(cell, D, [sh])
-        dt = time.perf_counter() - t
+        full_s, det = oracle_sample(cell, D, n_bra=8)
         if i >= args.warmup:
-            times.append(dt)
-    per_row = sum(times) / len(times)
-    full = per_row * nsh
+            fulls.append(full_s)
+            samples.append(time.perf_counter() - t)
+    full = statistics.mean(fulls)
     value = 1.0 / full
     out = {
         "metric": METRIC, "value": value, "unit": "builds/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_row * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "host cores (OpenMP)", "l2": "n/a"},
+        "config": {"workload": WORKLOADS[args.workload][0], "parallelism": "host cores (OpenMP)", "l2": "n/a"},
         "cpu_baseline": {"value": value, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": "J+K rows of one shell per step (shells %s), full build = mean row time x %d shells"
-                                   % (sample_shells, nsh)},
+                         "sample": "per step: 8 strided bra local pairs of %d against all kets plus 2 of %d G vectors, "
+                                   "extrapolated to a full build (%.1f s of CPU work per step)"
+                                   % (det["local_pairs"], det["n_g"], statistics.mean(samples))},
         "e2e": {"value": value, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
     return 0
 
 
-def cpu_baseline_sample(cell, budget_s=20.0):
-    """Oracle time for J+K rows of sampled shells (bounded), extrapolated."""
+def cpu_baseline_sample(cell, D):
+    """The oracle timed on a bounded sample of the same build (about 10-30 s)."""
     from oracle import oracle as O
 
-    D = O.density(cell)
-    t0 = time.perf_counter()
-    shells = []
-    for sh in [2, 11, 4, 20]:
-        O.jk_rows(cell, D, [sh])
-        shells.append(sh)
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = (time.perf_counter() - t0) / len(shells)
-    return {"value": 1.0 / (dt * len(cell.shells)), "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": "J+K rows of shells %s of the water box (%.1f s each), extrapolated to all %d shells"
-                      % (shells, dt, len(cell.shells))}
+    t = time.perf_counter()
+    full_s, det = oracle_sample(cell, D)
+    took = time.perf_counter() - t
+    return {"value": 1.0 / full_s, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d strided bra local pairs of %d against all kets and 2 of %d G vectors (%.1f s), extrapolated to a "
+                      "full J+K build (%.0f s)" % (det["bra_sampled"], det["local_pairs"], det["n_g"], took, full_s)}
+
+
+def run_serving(args):
+    """The serving stream (Poisson arrivals, per-request plans resident on the
+    device, iterations submitted one after another with perturbed densities)
+    through the library's request server.  Prints one JSON line per precision."""
+    import threading
+
+    import torch
+
+    import synthcells as sc
+    from paper_2410_22278_gb300 import jk
+
+    reqs = [r for r in sc.serving_requests(256) if r.natom_target <= args.max_atoms][: args.requests]
+    dev = torch.device("cuda:0")
+    results = {}
+    for prec, pname in ((jk.JK_MIXED, "mixed"), (jk.JK_FP64, "fp64")):
+        srv = jk.Server(device=0, hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)), max_slots=args.slots)
+        lat_build, lat_req = [], []
+        lock = threading.Lock()
+        t0 = time.perf_counter()
+
+        def serve(r):
+            arrive = t0 + (r.arrival_s - reqs[0].arrival_s)
+            time.sleep(max(0.0, arrive - time.perf_counter()))
+            t_arr = time.perf_counter()
+            cell = r.cell
+            plan = jk.plan_from_cell(cell, precision=prec)
+            n = cell.nbf
+            S = torch.empty((n, n), dtype=torch.float64, device=dev)
+            plan.overlap(S.data_ptr(), 0)
+            torch.cuda.synchronize()
+            D0 = sc.density_from_overlap(cell.orbital_guess(), S.cpu().numpy())
+            J = torch.empty((n, n), dtype=torch.float64, device=dev)
+            K = torch.empty_like(J)
+            for it in range(r.n_iter):
+                Dk = torch.from_numpy(D0 + sc.density_perturbation((r.rid << 8) + it, n)).to(dev)
+                torch.cuda.synchronize()
+                tk = srv.submit(plan, Dk.data_ptr(), J.data_ptr(), K.data_ptr())
+                st, lat = srv.wait(tk)
+                assert st == 0
+                with lock:
+                    lat_build.append(lat)
+            with lock:
+                lat_req.append(time.perf_counter() - t_arr)
+            plan.close()
+
+        threads = [threading.Thread(target=serve, args=(r,)) for r in reqs]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        wall = time.perf_counter() - t0
+        srv.close()
+        results[pname] = {"builds": len(lat_build), "builds_per_s": len(lat_build) / wall, "wall_s": wall,
+                          "build_latency_ms": {"p50": 1e3 * float(np.percentile(lat_build, 50)),
+                                               "p99": 1e3 * float(np.percentile(lat_build, 99))},
+                          "request_latency_s": {"p50": float(np.percentile(lat_req, 50)), "p99": float(np.percentile(lat_req, 99))}}
+    out = {"metric": METRIC, "mode": "serving", "requests": len(reqs), "max_atoms": args.max_atoms, "slots": args.slots,
+           "arrival_rate_per_s": 50.0, "data": "synthetic (serving stream: Poisson 50/s, diamond/water 50/50, 3-20 iterations, "
+           "|E_k|_F = 1e-3; requests above max_atoms skipped)", **results}
+    print(json.dumps(out))
+    return 0
 
 
 def aggregate(rank_times_ms, steps, world):
@@ -168,9 +232,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="water64", choices=sorted(WORKLOADS))
     ap.add_argument("--profile", action="store_true", help="mixed builds only (for ncu captures)")
+    ap.add_argument("--serving", action="store_true", help="run the serving stream instead of the single-cell build")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--max-atoms", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--hbm-budget-gb", type=float, default=64.0)
+    ap.add_argument("--autotune-cache", default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
 
@@ -207,6 +279,8 @@ def main():
     def build(p):
         p.build(D.data_ptr(), J.data_ptr(), K.data_ptr(), st)
 
+    # tile shapes of the real-space kernels chosen by the library's autotuner (outside the timed region)
+    tiles = plan.autotune(D.data_ptr(), st, args.autotune_cache)
     for _ in range(args.warmup):
         build(plan)
     stream.synchronize()
@@ -278,10 +352,8 @@ def main():
 
     pk, pk_kind = peaks()
     launches = sum(v[1] for k2, v in phases.items() if k2 != "total")
-    # dominant phase of the mixed build and its roofline
-    dom = max((k2 for k2 in phases if k2 != "total"), key=lambda k2: phases[k2][0])
     nq = info["n_quartets_schwarz"]
-    roof = roofline(dom, phases, info, counts, pk, pk_kind, n)
+    roof, roof_other = roofline(phases, pk, pk_kind)
     out = {
         "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -293,34 +365,48 @@ def main():
         "image_quartets_evaluated_per_s": (counts[0] + counts[1]) / (ms_per_step / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "fp64": {"builds_per_s": 1e3 / statistics.mean(e64), "ms_per_build": statistics.mean(e64),
-                 "phases_ms": {k2: v[0] for k2, v in phases64.items()}},
+                 "phases_ms": {k2: v[0] for k2, v in phases64.items() if k2 != "mma_flops"}},
         "mixed_vs_fp64": {"max_abs_dJ": float(np.abs(Jm - J64).max()), "max_abs_dK": float(np.abs(Km - K64).max()),
                           "dE_Ha": (ej + ek) - (ej64 + ek64), "E_J": ej64, "E_K": ek64},
-        "phases_ms": {k2: v[0] for k2, v in phases.items()},
+        "phases_ms": {k2: v[0] for k2, v in phases.items() if k2 != "mma_flops"},
         "fp64_fraction": counts[0] / max(1, counts[0] + counts[1]),
+        "autotuned_tiles": tiles,
         "gpu_launches": launches * args.steps,
         "roofline": roof,
+        "roofline_other": roof_other,
         "clocks": cl,
         "e2e": {"value": 1.0 / e2e_s, "unit": "builds/s", "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8},
     }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline_sample(cell)
+        from oracle import oracle as O
+
+        # the oracle's inputs come from the oracle's own overlap metric
+        out["cpu_baseline"] = cpu_baseline_sample(cell, O.density(cell))
     print(json.dumps(out))
     if dist:
         tdist.destroy_process_group()
     return 0
 
 
-def roofline(dom, phases, info, counts, pk, pk_kind, n):
-    ms = phases[dom][0] / max(1, phases[dom][1]) if phases[dom][1] else phases[dom][0]
-    if dom == "recip_k":
-        # K_LR GEMMs: 2 products of 2 n^3 flops per (G, real/imag) -> 8 n^3 per G
-        flops = 8.0 * n ** 3 * info["n_g"] / max(1, phases[dom][1] // 2)
-        ach = flops / (ms / 1e3) / 1e12
-        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")) / 2.0 * 0 + 1.25 if False else 1.25
-        return {"bound": "tensor", "kernel": "reciprocal exchange GEMMs (cuBLAS FP64 emulation)", "achieved": ach,
-                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_kind": "nominal FP64"}
-    return {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
+def roofline(phases, pk, pk_kind):
+    """Roofline of the dominant kernel family of a mixed build, from the
+    library's CUDA events on the build stream (phase sums over the timed
+    build) and the work each launch issues."""
+    gemm_ms, gemm_n = phases.get("tensor_gemm", (0.0, 0))
+    real_ms, real_n = phases["real_space"]
+    out = []
+    if gemm_ms > 0:
+        flops = phases["mma_flops"][0]
+        ach = flops / (gemm_ms / 1e3) / 1e12
+        peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+        out.append({"bound": "tensor", "kernel": "k_ozaki_gemm (split-precision BF16 MMA)", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": gemm_n,
+                    "ms_per_launch": gemm_ms / max(1, gemm_n),
+                    "peak_kind": "%s sustained bf16 (MEASURED_PEAKS.json)" % pk_kind, "work": "BF16 MMA flops issued"})
+    out.append({"bound": "alu", "kernel": "k_real / k_real_list (real-space quartets)", "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None, "launches": real_n, "ms": real_ms})
+    out.sort(key=lambda r: -(r.get("ms_per_launch", 0) * r.get("launches", 0) if r["bound"] == "tensor" else r.get("ms", 0)))
+    return out[0], out[1:]
 
 
 if __name__ == "__main__":

@@ -152,9 +152,21 @@ int jk_energy(const jk_plan *plan, const double *D, const double *J, const doubl
  * scaling, zeroing), ms[1] real-space quartet kernels, ms[2] reciprocal
  * structure factors, ms[3] reciprocal Coulomb contraction, ms[4]
  * reciprocal exchange contraction, ms[5] background and assembly, ms[6]
- * whole build; launches[0..6] the number of kernel launches per phase.
- * n = number of slots the caller provides (<= 7 used). */
+ * whole build, ms[7] the tensor-core GEMM launches inside ms[4] (mixed
+ * precision), ms[8] their operand slicing, ms[9] (not a time) the BF16 MMA
+ * flops those GEMMs issued; launches[i] the kernel launches per phase.
+ * n = number of slots the caller provides (<= 10 used). */
 int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
+
+/* Autotuner (no counterpart in the paper): choose the tile shape (kets
+ * per tile) of every real-space class-pair kernel by timing candidates
+ * {8, 16, 32, 64, 128} on a sub-range of bras with CUDA events, on
+ * `cuda_stream`, using density D (device, as in jk_build) for realistic
+ * work.  If cache_path is not NULL, choices are read from and written to
+ * that text file, keyed by GPU name, precision, class pair and size
+ * bucket.  chosen (may be NULL) receives up to 21 choices in class-pair
+ * order.  Overwrites the plan's build workspace; synchronises the stream. */
+int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *cache_path, int *chosen);
 
 /* Work counters of the most recent jk_build (waits for it to finish):
  * counts[0] unique image quartets evaluated in real space in FP64,

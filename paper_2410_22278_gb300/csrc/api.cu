@@ -159,6 +159,20 @@ int jk_build_times(jk_plan *plan, double *ms, int *launches, int n)
     return jk::build_times(plan->p, ms, launches, n);
 }
 
+int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *cache_path, int *chosen)
+{
+    if (!plan || !D) return fail(JK_ERR_INVALID, "plan or D is NULL");
+    try {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        cudaStreamWaitEvent(st, plan->done, 0);
+        int rc = jk::autotune(plan->p, D, st, cache_path, chosen);
+        cudaEventRecord(plan->done, st);
+        return rc;
+    } catch (...) {
+        return fail(JK_ERR_INVALID, "unexpected host exception");
+    }
+}
+
 int jk_build_counts(jk_plan *plan, long long *counts, int n)
 {
     if (!plan || !counts || n < 0) return fail(JK_ERR_INVALID, "bad arguments");

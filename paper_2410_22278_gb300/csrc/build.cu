@@ -14,6 +14,9 @@
 //      -(pi/(V w^2)) S D' S.
 //   5. J = F o (X + X^T + J_LR + J_bg), K = F o (Y + Y^T + K_LR + K_bg).
 #include <algorithm>
+#include <cstdio>
+#include <map>
+#include <string>
 
 #include "kernels.cuh"
 #include "launch.h"
@@ -180,6 +183,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     const bool mixed = P->precision == JK_MIXED;
     PhaseTimer &tm = P->timer;
     tm.begin(st);
+    w.mma_flops = 0;
     const int ev_all = tm.start(6);
     int ev = tm.start(0);
 
@@ -199,6 +203,10 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     if (w.nbig) cudaMemsetAsync(w.nbig, 0, 2 * sizeof(unsigned), st);
     int rc;
     if ((rc = cuda_check("prologue"))) return rc;
+    // mixed precision: slices of D' and the eigendecomposition of D' for the
+    // exchange contraction, enqueued now so they overlap nothing and are
+    // ready when the reciprocal phase needs them
+    if (mixed && K && (rc = ozaki_begin(P, st))) return rc;
     tm.stop(0, ev, mixed ? 4 : 1);
 
     // ---- real space
@@ -215,7 +223,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             a.k0 = Kc.b0;
             a.k1 = Kc.b1;
             a.same = cb == ck;
-            a.kchunk = 32;
+            a.kchunk = P->kchunk[cb][ck];
             a.tau = P->mixed_tau;
             a.Dp = w.Dp;
             a.dmax = w.dmax;
@@ -254,7 +262,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
 
     // ---- reciprocal space
     const int ng = (int)(P->gvec.size() / 4);
-    if (mixed && K && (rc = ozaki_slice_density(P, st))) return rc;
+    if (mixed && K && (rc = ozaki_prepare_lowrank(P, st))) return rc;
     for (int g0 = 0; g0 < ng; g0 += w.gc) {
         const int gcur = std::min(w.gc, ng - g0);
         ev = tm.start(2);
@@ -277,7 +285,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             ev = tm.start(4);
             if (mixed) {
                 // split-precision BF16 tensor-core GEMMs (about 42 significant bits)
-                if ((rc = ozaki_exchange_chunk(P, m2, w.Ds, w.Dex, st))) return rc;
+                if ((rc = ozaki_exchange_chunk(P, m2, st))) return rc;
                 tm.stop(4, ev, 4);
             } else {
                 // the plain FP64 form: K_LR += [M_1 .. M_2g] [Z_1; ..; Z_2g], Z_b = D' M_b (native DGEMM)
@@ -302,6 +310,111 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     tm.stop(5, ev, K ? 4 : 2);
     tm.stop(6, ev_all, 0);
     return cuda_check("epilogue");
+}
+
+// Autotuner: for every class pair with work, time the real-space tile
+// kernel of the plan's precision over a sub-range of at most 4096 bras
+// against all kets, for ket-chunk sizes {8, 16, 32, 64, 128}, and keep the
+// fastest.  Results are cached in a text file (one line per GPU name,
+// precision, class pair and size bucket) when cache_path is given.
+int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, int *chosen)
+{
+    std::lock_guard<std::mutex> guard(P->build_mu);
+    if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, P->device);
+    const bool mixed = P->precision == JK_MIXED;
+    const int n = P->nbf;
+    const size_t n2 = (size_t)n * n;
+    Workspace &w = P->ws;
+    PlanDev pl = P->dev();
+    k_scale<<<grid_for(n2), 256, 0, st>>>(n, P->d_compf, D, w.Dp);
+    if (mixed) k_to_float<<<grid_for(n2), 256, 0, st>>>(n2, w.Dp, w.Dpf);
+    // existing cache entries
+    std::map<std::string, int> cache;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char key[512];
+            int v;
+            while (fscanf(f, "%511s %d", key, &v) == 2) cache[key] = v;
+            fclose(f);
+        }
+    }
+    auto bucket = [](int x) { int b = 0; while ((1 << b) < x) ++b; return b; };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cands[] = {8, 16, 32, 64, 128};
+    int k = 0;
+    bool dirty = false;
+    for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
+        for (int ck = cb; ck < JK_NCLASS_MAX; ++ck) {
+            const ClassRange &B = P->classes[cb], &Kc = P->classes[ck];
+            if (B.b1 <= B.b0 || Kc.b1 <= Kc.b0) continue;
+            char key[512];
+            snprintf(key, sizeof key, "%s|%s|%d%d|%d|%d", prop.name, mixed ? "mixed" : "fp64", cb, ck, bucket(B.b1 - B.b0),
+                     bucket(Kc.b1 - Kc.b0));
+            for (char *q = key; *q; ++q)
+                if (*q == ' ') *q = '_';
+            int best = -1;
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                best = it->second;
+            } else {
+                float best_ms = 1e30f;
+                for (int c : cands) {
+                    RealLaunch a{};
+                    a.pl = pl;
+                    a.b0 = B.b0;
+                    a.b1 = std::min(B.b1, B.b0 + 4096);
+                    a.k0 = Kc.b0;
+                    a.k1 = Kc.b1;
+                    a.same = cb == ck;
+                    a.kchunk = c;
+                    a.mode = 0;
+                    a.fp32 = mixed;
+                    a.Dp = w.Dp;
+                    a.dmax = w.dmax;
+                    a.Dpf = w.Dpf;
+                    a.dmaxf = w.dmaxf;
+                    a.X = w.X;
+                    a.Y = w.Y;
+                    a.cnt = w.cnt;
+                    a.st = st;
+                    cudaEventRecord(e0, st);
+                    launch_real(cb, ck, a);
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return fail(JK_ERR_CUDA, "autotune launch failed");
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
+                }
+                cache[key] = best;
+                dirty = true;
+            }
+            P->kchunk[cb][ck] = best;
+            if (chosen && k < 36) chosen[k] = best;
+            ++k;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cache_path && dirty) {
+        FILE *f = fopen(cache_path, "w");
+        if (f) {
+            for (auto &kv : cache) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+            fclose(f);
+        }
+    }
+    P->tuned = true;
+    return cuda_check("autotune");
 }
 
 int build_counts(Plan *P, long long *counts, int n)
@@ -337,6 +450,7 @@ int build_times(Plan *P, double *ms, int *launches, int n)
     int tot = 0;
     for (int i = 0; i < 6; ++i) tot += tm.launches[i];
     if (launches && n > 6) launches[6] = tot;
+    if (ms && n > 9) ms[9] = P->ws.mma_flops;  // slot 9: BF16 MMA flops issued (for the tensor roofline)
     return JK_OK;
 }
 

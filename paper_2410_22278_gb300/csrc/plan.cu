@@ -252,7 +252,7 @@ static int alloc_ws(Plan *P)
     int ng = (int)(P->gvec.size() / 4);
     const bool mixed = P->precision == JK_MIXED;
     if (mixed) {
-        w.oz_slices = 6;  // 7-bit slices: about 42 significant bits per operand
+        w.oz_slices = 5;  // 7-bit slices: about 35 significant bits per operand
         w.npad = (P->nbf + 127) / 128 * 128;
     }
     // per G: the structure-factor slab M and its GEMM partner Z (2 n^2 doubles
@@ -286,9 +286,19 @@ static int alloc_ws(Plan *P)
             bytes += count * sizeof(int);
             return true;
         };
-        if (!alb(&w.Ms, 2 * (size_t)gc * sl) || !alb(&w.Zs, 2 * (size_t)gc * sl) || !alb(&w.Ds, sl) ||
-            !ali(&w.Mex, 2 * (size_t)gc * w.npad) || !ali(&w.Zex, 2 * (size_t)gc * w.npad) || !ali(&w.Dex, w.npad))
+        if (!alb(&w.Ms, 2 * (size_t)gc * sl) || !alb(&w.Zs, 2 * (size_t)gc * sl) || !alb(&w.Ds, sl) || !alb(&w.Cs, sl) ||
+            !ali(&w.Mex, 2 * (size_t)gc * w.npad) || !ali(&w.Zex, 2 * (size_t)gc * w.npad) || !ali(&w.Dex, w.npad) ||
+            !ali(&w.Cex, w.npad) || !ali(&w.eigIdx, w.npad) || !ali(&w.eigInfo, 1) || !al(&w.eigV, n2) || !al(&w.eigW, P->nbf) ||
+            !al(&w.Ct, (size_t)w.npad * P->nbf))
             return fail(JK_ERR_OOM, "cudaMalloc failed for tensor-core exchange workspace");
+        // eigensolver for the low-rank form of D (closed-shell densities have rank n_occ)
+        if (cusolverDnCreate(&w.solver) != CUSOLVER_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cusolverDnCreate failed");
+        if (cusolverDnDsyevd_bufferSize(w.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, P->nbf, w.eigV, P->nbf, w.eigW,
+                                        &w.eigLwork) != CUSOLVER_STATUS_SUCCESS)
+            return fail(JK_ERR_CUDA, "cusolverDnDsyevd_bufferSize failed");
+        if (!al(&w.eigWork, (size_t)std::max(1, w.eigLwork))) return fail(JK_ERR_OOM, "cudaMalloc failed for eigensolver");
+        if (cudaMallocHost((void **)&w.eigW_host, sizeof(double) * P->nbf) != cudaSuccess) return fail(JK_ERR_OOM, "pinned buffer");
+        if (cudaEventCreateWithFlags(&w.eig_done, cudaEventDisableTiming) != cudaSuccess) return fail(JK_ERR_CUDA, "event");
     }
     if (cudaMalloc((void **)&w.err, sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
     if (cudaMalloc((void **)&w.cnt, 4 * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
@@ -327,6 +337,8 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
             if (!std::isfinite(sh.center[k])) return fail(JK_ERR_INVALID, "centre not finite");
     }
     Plan *P = new Plan();
+    for (int i = 0; i < JK_NCLASS_MAX; ++i)
+        for (int j = 0; j < JK_NCLASS_MAX; ++j) P->kchunk[i][j] = 32;
     P->device = device;
     P->precision = precision;
     memcpy(P->L, cell->lattice, sizeof P->L);
@@ -727,10 +739,14 @@ void destroy_plan(Plan *P)
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
                     P->d_g0, P->d_compf, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
                     P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
-                    P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf};
+                    P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex,
+                    P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P->blas) cublasDestroy(P->blas);
+    if (P->ws.solver) cusolverDnDestroy(P->ws.solver);
+    if (P->ws.eigW_host) cudaFreeHost(P->ws.eigW_host);
+    if (P->ws.eig_done) cudaEventDestroy(P->ws.eig_done);
     P->timer.destroy();
     delete P;
 }

@@ -1,6 +1,8 @@
 // Host-side plan: built once per geometry (Section 3.1), then immutable.
 #pragma once
 #include <cublas_v2.h>
+#include <cusolverDn.h>
+#include <cmath>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -45,13 +47,22 @@ struct Workspace {
     size_t bytes = 0;
     // split-precision tensor-core exchange (mixed precision)
     int npad = 0, oz_slices = 0;
-    __nv_bfloat16 *Ms = nullptr, *Zs = nullptr, *Ds = nullptr;
-    int *Mex = nullptr, *Zex = nullptr, *Dex = nullptr;
+    __nv_bfloat16 *Ms = nullptr, *Zs = nullptr, *Ds = nullptr, *Cs = nullptr;
+    int *Mex = nullptr, *Zex = nullptr, *Dex = nullptr, *Cex = nullptr;
+    // low-rank form of D (eigendecomposition on the device)
+    cusolverDnHandle_t solver = nullptr;
+    double *eigV = nullptr, *eigW = nullptr, *eigWork = nullptr, *eigW_host = nullptr, *Ct = nullptr;
+    int *eigInfo = nullptr, *eigIdx = nullptr;
+    int eigLwork = 0;
+    cudaEvent_t eig_done = nullptr;
+    bool lowrank = false;
+    int rpos = 0, rneg = 0;
+    double mma_flops = 0;  // BF16 MMA flops issued by the split-precision GEMMs of the last build
 };
 
 // CUDA events bracketing the phases of one build (see jk_build_times)
 struct PhaseTimer {
-    static constexpr int kPhases = 7;
+    static constexpr int kPhases = 9;  // 0..6 as in jk_build_times, 7 tensor-core GEMMs, 8 their operand slicing
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<int, int>>> marks;  // phase, (start event, end event)
     int next = 0;
@@ -84,6 +95,8 @@ struct Plan {
     long long n_ord_shell_pairs = 0, n_ord_prim_pairs = 0, n_ord_local_pairs = 0;
     long long n_shell_pairs = 0, n_quartets = 0, n_quartets_schwarz = 0, n_quartets_fp64 = 0;
     double mixed_tau = 0;
+    int kchunk[JK_NCLASS_MAX][JK_NCLASS_MAX];  // kets per tile of the real-space kernels (autotuned)
+    bool tuned = false;
     // device arrays
     ShellRec *d_shells = nullptr;
     SpiRec *d_spi = nullptr;
@@ -114,8 +127,10 @@ int run_build(Plan *p, const double *D, double *J, double *K, cudaStream_t st);
 int compute_overlap_raw(Plan *p, cudaStream_t st);
 int build_times(Plan *p, double *ms, int *launches, int n);
 int build_counts(Plan *p, long long *counts, int n);
-int ozaki_exchange_chunk(Plan *P, int m2, const __nv_bfloat16 *Ds, const int *Dex, cudaStream_t st);
-int ozaki_slice_density(Plan *P, cudaStream_t st);
+int autotune(Plan *p, const double *D, cudaStream_t st, const char *cache_path, int *chosen);
+int ozaki_begin(Plan *P, cudaStream_t st);
+int ozaki_prepare_lowrank(Plan *P, cudaStream_t st);
+int ozaki_exchange_chunk(Plan *P, int m2, cudaStream_t st);
 
 // host helpers shared by plan.cu and api.cu
 void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out);

@@ -32,7 +32,7 @@ JK_MIXED = 1
 
 # every symbol declared in include/jk.h
 EXPORTS = [
-    "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_build_counts", "jk_energy",
+    "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_build_counts", "jk_autotune", "jk_energy",
     "jk_overlap", "jk_ewald_point_charges", "jk_server_create", "jk_submit", "jk_wait", "jk_server_destroy",
     "jk_status_string", "jk_last_error", "jk_microbench_fma",
 ]
@@ -95,6 +95,7 @@ def lib():
         L.jk_build_host.argtypes = [vp, dp, dp, dp, vp]
         L.jk_build_times.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         L.jk_build_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+        L.jk_autotune.argtypes = [vp, vp, vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
         L.jk_energy.argtypes = [vp, vp, vp, vp, dp, dp, vp]
         L.jk_overlap.argtypes = [vp, vp, vp]
         L.jk_ewald_point_charges.argtypes = [ctypes.POINTER(jk_cell), ctypes.c_int, dp, dp, ctypes.c_double,
@@ -208,14 +209,24 @@ class Plan:
         _check(lib().jk_build_host(self._h, _dp(D), _dp(J) if J is not None else None, _dp(K) if K is not None else None,
                                    stream or None), "jk_build_host")
 
-    PHASES = ["prologue", "real_space", "recip_sfac", "recip_j", "recip_k", "epilogue", "total"]
+    PHASES = ["prologue", "real_space", "recip_sfac", "recip_j", "recip_k", "epilogue", "total", "tensor_gemm", "tensor_slice"]
 
     def build_times(self):
-        """{phase: (ms, launches)} of the most recent build (device events)."""
-        ms = (ctypes.c_double * 7)()
-        nl = (ctypes.c_int * 7)()
-        _check(lib().jk_build_times(self._h, ms, nl, 7), "jk_build_times")
-        return {p: (ms[i], nl[i]) for i, p in enumerate(self.PHASES)}
+        """{phase: (ms, launches)} of the most recent build (device events),
+        plus "mma_flops": BF16 MMA flops issued by the tensor-core GEMMs."""
+        ms = (ctypes.c_double * 10)()
+        nl = (ctypes.c_int * 10)()
+        _check(lib().jk_build_times(self._h, ms, nl, 10), "jk_build_times")
+        out = {p: (ms[i], nl[i]) for i, p in enumerate(self.PHASES)}
+        out["mma_flops"] = (ms[9], 0)
+        return out
+
+    def autotune(self, D_ptr: int, stream: int = 0, cache_path: str = None):
+        """Tile shapes of the real-space kernels chosen by timing (jk_autotune)."""
+        chosen = (ctypes.c_int * 36)()
+        _check(lib().jk_autotune(self._h, D_ptr, stream or None, cache_path.encode() if cache_path else None, chosen),
+               "jk_autotune")
+        return [c for c in chosen if c]
 
     def build_counts(self):
         """(FP64 image quartets, FP32 image quartets) of the most recent build."""
