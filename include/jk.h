@@ -146,6 +146,32 @@ int jk_build_host(jk_plan *plan, const double *D_host, double *J_host, double *K
 int jk_energy(const jk_plan *plan, const double *D, const double *J, const double *K, double *e_coul, double *e_exch,
               void *cuda_stream);
 
+/* jk_energy without any device allocation (the paper has no counterpart;
+ * this is a deployment variant of the energy reduction above).  For callers
+ * that must not have a library allocate device memory: a framework whose
+ * pool allocator owns the device memory under a fixed budget (a foreign
+ * cudaMalloc may fail there or fragment the pool), or a latency-bound loop
+ * that cannot pay for an allocation or free inside the call, which may
+ * synchronise the whole device.  Same arguments, results and
+ * synchronisation as jk_energy; the sums are taken in a different order, so
+ * the two agree to FP64 rounding, not bit for bit.
+ *
+ * Scratch: a fixed 64 KB device array inside the library (4096 block
+ * partials and the two sums), present on every device the library is loaded
+ * on until the process exits.  Nothing in it has to start at zero: every
+ * value a call reads was written earlier in the same call.
+ * Limit: nbf <= 16384; a larger plan returns JK_ERR_INVALID with a message
+ * naming the limit (use jk_energy there).
+ * First call on a device: looks up the array's device address once
+ * (cudaGetSymbolAddress with the plan's device current); make that first
+ * call before any stream capture begins.
+ * Concurrency: all calls on one device share the array, so two calls whose
+ * work overlaps on the GPU (different streams or host threads) race and may
+ * return wrong sums; serialise them.
+ * Errors: JK_ERR_INVALID (NULL argument, nbf above the limit), JK_ERR_CUDA. */
+int jk_energy_noalloc(const jk_plan *plan, const double *D, const double *J, const double *K, double *e_coul,
+                      double *e_exch, void *cuda_stream);
+
 /* Device time of each phase of the most recent jk_build on this plan, in
  * milliseconds, from CUDA events recorded on the build's stream around the
  * phase's kernels (waits for that build to finish).  ms[0] prologue (D

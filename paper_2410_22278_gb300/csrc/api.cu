@@ -226,6 +226,13 @@ int jk_energy(const jk_plan *plan, const double *D, const double *J, const doubl
     return JK_OK;
 }
 
+int jk_energy_noalloc(const jk_plan *plan, const double *D, const double *J, const double *K, double *e_coul, double *e_exch,
+                      void *cuda_stream)
+{
+    if (!plan || !D || !e_coul || !e_exch) return fail(JK_ERR_INVALID, "NULL argument");
+    return jk::energy_noalloc(plan->p, D, J, K, e_coul, e_exch, (cudaStream_t)cuda_stream);
+}
+
 __global__ void jk_scale_kernel(int n, const double *f, const double *A, double *B);
 
 int jk_overlap(const jk_plan *plan, double *S, void *cuda_stream)

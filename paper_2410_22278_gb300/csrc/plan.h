@@ -131,6 +131,8 @@ int autotune(Plan *p, const double *D, cudaStream_t st, const char *cache_path, 
 int ozaki_begin(Plan *P, cudaStream_t st);
 int ozaki_prepare_lowrank(Plan *P, cudaStream_t st);
 int ozaki_exchange_chunk(Plan *P, int m2, cudaStream_t st);
+int energy_noalloc(const Plan *P, const double *D, const double *J, const double *K, double *e_coul, double *e_exch,
+                   cudaStream_t st);
 
 // host helpers shared by plan.cu and api.cu
 void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out);

@@ -33,6 +33,7 @@ JK_MIXED = 1
 # every symbol declared in include/jk.h
 EXPORTS = [
     "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_build_counts", "jk_autotune", "jk_energy",
+    "jk_energy_noalloc",
     "jk_overlap", "jk_ewald_point_charges", "jk_server_create", "jk_submit", "jk_wait", "jk_server_destroy",
     "jk_status_string", "jk_last_error", "jk_microbench_fma",
 ]
@@ -97,6 +98,7 @@ def lib():
         L.jk_build_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.jk_autotune.argtypes = [vp, vp, vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
         L.jk_energy.argtypes = [vp, vp, vp, vp, dp, dp, vp]
+        L.jk_energy_noalloc.argtypes = [vp, vp, vp, vp, dp, dp, vp]
         L.jk_overlap.argtypes = [vp, vp, vp]
         L.jk_ewald_point_charges.argtypes = [ctypes.POINTER(jk_cell), ctypes.c_int, dp, dp, ctypes.c_double,
                                              ctypes.c_double, dp]
@@ -238,6 +240,13 @@ class Plan:
         ej, ek = ctypes.c_double(), ctypes.c_double()
         _check(lib().jk_energy(self._h, D_ptr, J_ptr or None, K_ptr or None, ctypes.byref(ej), ctypes.byref(ek),
                                stream or None), "jk_energy")
+        return ej.value, ek.value
+
+    def energy_noalloc(self, D_ptr: int, J_ptr: int, K_ptr: int, stream: int = 0):
+        """jk_energy with the library's fixed device scratch: allocates nothing."""
+        ej, ek = ctypes.c_double(), ctypes.c_double()
+        _check(lib().jk_energy_noalloc(self._h, D_ptr, J_ptr or None, K_ptr or None, ctypes.byref(ej), ctypes.byref(ek),
+                                       stream or None), "jk_energy_noalloc")
         return ej.value, ek.value
 
     def overlap(self, S_ptr: int, stream: int = 0):
