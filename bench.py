@@ -307,6 +307,7 @@ def main():
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     phases = plan.build_times()  # last build's phase split (library events on the same stream)
     counts = plan.build_counts()
+    real_flops = plan.real_space_flops()
     if dist:
         t = torch.tensor([total_ms], device=dev)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
@@ -351,9 +352,9 @@ def main():
         return 0
 
     pk, pk_kind = peaks()
-    launches = sum(v[1] for k2, v in phases.items() if k2 != "total")
+    launches = phases["total"][1]  # the library's own kernel launches per build (phases 0-5)
     nq = info["n_quartets_schwarz"]
-    roof, roof_other = roofline(phases, pk, pk_kind)
+    roof, roof_other = roofline(phases, real_flops, pk, pk_kind, cl.get("sm_max_mhz") or 2070.0)
     out = {
         "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -388,24 +389,48 @@ def main():
     return 0
 
 
-def roofline(phases, pk, pk_kind):
-    """Roofline of the dominant kernel family of a mixed build, from the
-    library's CUDA events on the build stream (phase sums over the timed
-    build) and the work each launch issues."""
+FP32_LANES_PER_SM, N_SM = 128, 152
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (vector and tensor)
+
+
+def roofline(phases, real_flops, pk, pk_kind, sm_mhz_max):
+    """Roofline of each kernel family of a mixed build, from the library's
+    CUDA events on the build stream (phase sums over one build) and the work
+    the kernels tallied: real-space FP32 tile kernels and FP64 list kernels
+    (algorithmic flops of the McMurchie-Davidson steps, against the FP32 /
+    FP64 ALU peaks), split-precision GEMMs (BF16 MMA flops issued, against
+    the measured BF16 peak).  Returns the family with the most device time
+    first."""
+    fl64, fl32 = real_flops
+    real_ms = phases["real_space"][0]
+    list_ms, list_n = phases.get("real_fp64_list", (0.0, 0))
+    tile_ms = max(real_ms - list_ms, 1e-9)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    out = [
+        {"bound": "alu", "kernel": "k_real<..., float> (FP32 real-space quartet tiles)", "achieved": fl32 / (tile_ms / 1e3) / 1e12,
+         "peak": fp32_peak, "unit": "TFLOP/s", "frac": fl32 / (tile_ms / 1e3) / 1e12 / fp32_peak, "traffic": None,
+         "ms": tile_ms, "launches": phases["real_space"][1] - list_n,
+         "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 flops x %.0f MHz" % (N_SM, FP32_LANES_PER_SM, sm_mhz_max),
+         "work": "algorithmic flops of the MD steps (csrc/flops.h) tallied by the kernels"},
+    ]
+    if list_ms > 0:
+        ach = fl64 / (list_ms / 1e3) / 1e12
+        out.append({"bound": "alu", "kernel": "k_real_list (FP64 large quartets)", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "ms": list_ms, "launches": list_n,
+                    "peak_kind": "nominal GB300 FP64", "work": "algorithmic flops of the MD steps (csrc/flops.h)"})
     gemm_ms, gemm_n = phases.get("tensor_gemm", (0.0, 0))
-    real_ms, real_n = phases["real_space"]
-    out = []
     if gemm_ms > 0:
-        flops = phases["mma_flops"][0]
-        ach = flops / (gemm_ms / 1e3) / 1e12
+        ach = phases["mma_flops"][0] / (gemm_ms / 1e3) / 1e12
         peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
-        out.append({"bound": "tensor", "kernel": "k_ozaki_gemm (split-precision BF16 MMA)", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": gemm_n,
-                    "ms_per_launch": gemm_ms / max(1, gemm_n),
+        out.append({"bound": "tensor", "kernel": "k_ozaki_tc (split-precision BF16 tcgen05 GEMM)", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "ms": gemm_ms, "launches": gemm_n,
                     "peak_kind": "%s sustained bf16 (MEASURED_PEAKS.json)" % pk_kind, "work": "BF16 MMA flops issued"})
-    out.append({"bound": "alu", "kernel": "k_real / k_real_list (real-space quartets)", "achieved": None, "peak": None,
-                "unit": None, "frac": None, "traffic": None, "launches": real_n, "ms": real_ms})
-    out.sort(key=lambda r: -(r.get("ms_per_launch", 0) * r.get("launches", 0) if r["bound"] == "tensor" else r.get("ms", 0)))
+    sfac_ms, sfac_n = phases.get("recip_sfac", (0.0, 0))
+    out.append({"bound": "alu", "kernel": "k_sfac (structure factors)", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "ms": sfac_ms, "launches": sfac_n})
+    out.sort(key=lambda r: -r["ms"])
+    for r in out:
+        r["ms_per_launch"] = r["ms"] / max(1, r["launches"])
     return out[0], out[1:]
 
 

@@ -61,8 +61,8 @@ typedef struct {
 
 /* The four lattice-sum thresholds of Section 3.6 (values <= 0 select the
  * paper's default 1e-14) and the mixed-precision switch (Section 3.5):
- * a shell quartet whose density-weighted Schwarz estimate is at or above
- * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: automatic). */
+ * an image quartet whose density-weighted size estimate is at or above
+ * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: 1e-4). */
 typedef struct {
     double pair_R;   /* delta_pair-R, Eq. pbc_eri_pair_cutoff_implementation */
     double pair_cs;  /* delta_pair-Cauchy-Schwarz, Eq. pbc_eri_cauchy_schwarz_cutoff_implementation */
@@ -179,9 +179,10 @@ int jk_energy_noalloc(const jk_plan *plan, const double *D, const double *J, con
  * structure factors, ms[3] reciprocal Coulomb contraction, ms[4]
  * reciprocal exchange contraction, ms[5] background and assembly, ms[6]
  * whole build, ms[7] the tensor-core GEMM launches inside ms[4] (mixed
- * precision), ms[8] their operand slicing, ms[9] (not a time) the BF16 MMA
- * flops those GEMMs issued; launches[i] the kernel launches per phase.
- * n = number of slots the caller provides (<= 10 used). */
+ * precision), ms[8] their operand slicing, ms[9] the FP64 pass over the
+ * large quartets inside ms[1] (mixed precision), ms[10] (not a time) the
+ * BF16 MMA flops the GEMMs issued; launches[i] the kernel launches per
+ * phase.  n = number of slots the caller provides (<= 11 used). */
 int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
 
 /* Autotuner (no counterpart in the paper): choose the tile shape (kets
@@ -198,8 +199,12 @@ int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *c
  * counts[0] unique image quartets evaluated in real space in FP64,
  * counts[1] those evaluated in FP32 (mixed precision only), counts[2]
  * quartets that the mixed policy wanted in FP64 but that overflowed the
- * plan's FP64 list and were evaluated in FP32 (0 in a healthy build).
- * n <= 4. */
+ * plan's FP64 list and were evaluated in FP32 (0 in a healthy build),
+ * counts[3] 0, counts[4] and counts[5] the algorithmic floating-point
+ * operations of the real-space evaluation in FP64 and in FP32 (operation
+ * counts of the McMurchie-Davidson steps per evaluated lattice image,
+ * primitive quartet and image quartet).  n <= 6.  Returns JK_ERR_TIMEOUT
+ * (and the build's J and K are NaN) if a bounded device wait ran out. */
 int jk_build_counts(jk_plan *plan, long long *counts, int n);
 
 /* Gamma overlap over the plan's pair list (Eq. pbc_overlap_formula),

@@ -83,16 +83,18 @@ __global__ void k_dot2(size_t n2, const double *__restrict__ B, const double *__
 // J = F o (X + X^T + JLR + c tr S), K = F o (Y + Y^T + KLR + c SDS)
 __global__ void k_final(int n, const double *__restrict__ f, const double *__restrict__ X, const double *__restrict__ Y,
                         const double *__restrict__ JLR, const double *__restrict__ KLR, const double *__restrict__ S,
-                        const double *__restrict__ SDS, const double *__restrict__ trDS, double c, double *__restrict__ J,
-                        double *__restrict__ K)
+                        const double *__restrict__ SDS, const double *__restrict__ trDS, double c, const unsigned *__restrict__ err,
+                        double *__restrict__ J, double *__restrict__ K)
 {
     const size_t n2 = (size_t)n * n;
     const double tr = *trDS;
+    // a wait of a tensor-core GEMM ran out: the result is not trusted
+    const double poison = *err ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
         const size_t r = i / n, cidx = i % n, t = cidx * n + r;
         const double ff = f[r] * f[cidx];
-        if (J) J[i] = ff * (X[i] + X[t] + 0.5 * (JLR[i] + JLR[t]) + c * tr * S[i]);
-        if (K) K[i] = ff * (Y[i] + Y[t] + 0.5 * (KLR[i] + KLR[t]) + c * 0.5 * (SDS[i] + SDS[t]));
+        if (J) J[i] = ff * (X[i] + X[t] + 0.5 * (JLR[i] + JLR[t]) + c * tr * S[i]) + poison;
+        if (K) K[i] = ff * (Y[i] + Y[t] + 0.5 * (KLR[i] + KLR[t]) + c * 0.5 * (SDS[i] + SDS[t])) + poison;
     }
 }
 
@@ -199,7 +201,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     cudaMemsetAsync(w.JLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.KLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), st);
-    cudaMemsetAsync(w.cnt, 0, 4 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(w.cnt, 0, 8 * sizeof(unsigned long long), st);
     if (w.nbig) cudaMemsetAsync(w.nbig, 0, 2 * sizeof(unsigned), st);
     int rc;
     if ((rc = cuda_check("prologue"))) return rc;
@@ -252,7 +254,9 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
                 // ... then FP64 over the compact list
                 a.list_pass = true;
                 a.cnt64 = w.cnt;
+                const int el = tm.start(9);
                 launch_real(cb, ck, a);
+                tm.stop(9, el, 1);
                 nreal += 2;
             }
             if ((rc = cuda_check("real-space kernel"))) return rc;
@@ -284,8 +288,8 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
         if (K) {
             ev = tm.start(4);
             if (mixed) {
-                // split-precision BF16 tensor-core GEMMs (about 42 significant bits)
-                if ((rc = ozaki_exchange_chunk(P, m2, st))) return rc;
+                // split-precision BF16 tensor-core GEMMs, slices per chunk from its G bound
+                if ((rc = ozaki_exchange_chunk(P, m2, w.chunk_slices[g0 / w.gc], st))) return rc;
                 tm.stop(4, ev, 4);
             } else {
                 // the plain FP64 form: K_LR += [M_1 .. M_2g] [Z_1; ..; Z_2g], Z_b = D' M_b (native DGEMM)
@@ -295,6 +299,11 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
                 tm.stop(4, ev, 2);
             }
         }
+    }
+    if (mixed && K) {
+        ev = tm.start(4);
+        if ((rc = ozaki_finish(P, st))) return rc;
+        tm.stop(4, ev, 1);
     }
     ev = tm.start(5);
 
@@ -306,7 +315,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
         BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, w.Dp, n, P->d_S, n, &zero, w.T1, n));
         BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, P->d_S, n, w.T1, n, &zero, w.T2, n));
     }
-    k_final<<<grid_for(n2), 256, 0, st>>>(n, P->d_compf, w.X, w.Y, w.JLR, w.KLR, P->d_S, w.T2, w.scal, cbg, J, K);
+    k_final<<<grid_for(n2), 256, 0, st>>>(n, P->d_compf, w.X, w.Y, w.JLR, w.KLR, P->d_S, w.T2, w.scal, cbg, w.err, J, K);
     tm.stop(5, ev, K ? 4 : 2);
     tm.stop(6, ev_all, 0);
     return cuda_check("epilogue");
@@ -419,7 +428,7 @@ int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, 
 
 int build_counts(Plan *P, long long *counts, int n)
 {
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned hb[2] = {0, 0};
     if (P->timer.next > 0 && cudaEventSynchronize(P->timer.pool[P->timer.next - 1]) != cudaSuccess)
         return fail(JK_ERR_CUDA, "build did not finish");
@@ -427,7 +436,11 @@ int build_counts(Plan *P, long long *counts, int n)
     if (P->ws.nbig && cudaMemcpy(hb, P->ws.nbig, sizeof hb, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(JK_ERR_CUDA, "count copy failed");
     h[2] = hb[1];
-    for (int i = 0; i < n && i < 4; ++i) counts[i] = (long long)h[i];
+    h[3] = 0;
+    for (int i = 0; i < n && i < 6; ++i) counts[i] = (long long)h[i];
+    unsigned e = 0;
+    if (cudaMemcpy(&e, P->ws.err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(JK_ERR_CUDA, "check word copy failed");
+    if (e) return fail(JK_ERR_TIMEOUT, "a bounded wait in a tensor-core GEMM ran out; J and K of that build are NaN");
     return JK_OK;
 }
 
@@ -450,7 +463,7 @@ int build_times(Plan *P, double *ms, int *launches, int n)
     int tot = 0;
     for (int i = 0; i < 6; ++i) tot += tm.launches[i];
     if (launches && n > 6) launches[6] = tot;
-    if (ms && n > 9) ms[9] = P->ws.mma_flops;  // slot 9: BF16 MMA flops issued (for the tensor roofline)
+    if (ms && n > 10) ms[10] = P->ws.mma_flops;  // slot 10: BF16 MMA flops issued (for the tensor roofline)
     return JK_OK;
 }
 

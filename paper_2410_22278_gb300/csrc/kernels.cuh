@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "jk_internal.h"
+#include "flops.h"
 #include "md.cuh"
 
 namespace jk {
@@ -104,6 +105,20 @@ __device__ __forceinline__ void seeds(float x2, float alpha, float aw, float cw,
     }
 }
 
+// Exact float -> double with integer operations only, for the FP64
+// digestion atomics of the FP32 kernels: a conversion instruction would run
+// on the FP64 pipe, which here has 1/64 of the FP32 rate.  Zero and
+// subnormal floats (below 1.2e-38, far under any digested term) give 0.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    const unsigned lo = u << 29;
+    return e ? __hiloint2double((int)hi, (int)lo) : 0.0;
+}
+
 // Pair data in the kernel's working precision.
 template <typename T>
 struct PairT {
@@ -145,7 +160,7 @@ __device__ __forceinline__ float lat_at(const PlanDev &pl, int k, float) { retur
 // kernels (they only decide which terms to form); the terms themselves are
 // formed in T.
 template <int LA, int LB, int LC, int LD, typename T>
-__device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk, T *V)
+__device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk, T *V, unsigned long long &fl)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int L = LA + LB + LC + LD, LAB = LA + LB, LCD = LC + LD;
@@ -160,6 +175,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
         load_pair(pl, sb.pp0 + i, xf, x);
         T Ea[3][(LA + 1) * (LB + 1) * NTA];
         const T oo2p = T(0.5) * x.ip;
+        fl += flops::per_bra_prim(LA, LB);
 #pragma unroll
         for (int k = 0; k < 3; ++k) herm_E<LA, LB, T>(x.PA[k], x.PB[k], oo2p, Ea[k]);
         for (int j = 0; j < sk.npp; ++j) {
@@ -207,6 +223,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
                 const T x2 = Xx * Xx + Xy * Xy + Xz * Xz;
                 if ((float)x2 >= r2) continue;
                 any = true;
+                fl += flops::per_image(L);
                 T s[L + 1];
                 seeds<L>(x2, alpha, aw, cw, pl, s);
                 T B[D * D * D];
@@ -219,6 +236,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
                         for (int v = 0; v <= L - t - u; ++v) Rs[(t * D + u) * D + v] += B[(t * D + u) * D + v];
             }
             if (!any) continue;
+            fl += flops::per_prim_quartet(LA, LB, LC, LD);
             T Ec[3][(LC + 1) * (LD + 1) * NTC];
             const T oo2q = T(0.5) * iq;
 #pragma unroll
@@ -338,6 +356,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
     const T dIJ = mode ? dmax[sb.I * nsh + sb.J] : T(0);
     const float tauf = (float)tau;
     unsigned nq = 0;
+    unsigned long long fl = 0;  // algorithmic flops (flops.h)
     for (int kt = kbeg; kt < kend; ++kt) {
         const SpiRec sk = pl.spi[kt];
         bool valid = act && (!same || kt >= bra);
@@ -358,8 +377,9 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
         T V[NA * NB * NC * ND];
 #pragma unroll
         for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = T(0);
-        if (valid) quartet_block<LA, LB, LC, LD, T>(pl, sb, sk, V);
+        if (valid) quartet_block<LA, LB, LC, LD, T>(pl, sb, sk, V, fl);
         nq += valid;
+        fl += valid ? flops::per_quartet(LA, LB, LC, LD) : 0;
         // orbit weight, exact in either precision
         const T w = valid ? T(sb.w) * T(sk.w) * ((same && kt == bra) ? T(0.5) : T(1)) : T(0);
         const int aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
@@ -383,7 +403,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
 #pragma unroll
             for (int ab = 0; ab < NA * NB; ++ab) s += V[ab * NC * ND + cd] * Dij[ab];
             s = warp_sum_t(T(2) * w * s);
-            if ((threadIdx.x & 31) == 0 && s != T(0)) atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, (double)s);
+            if ((threadIdx.x & 31) == 0 && s != T(0)) atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, to_f64(s));
         }
         // exchange: the four index assignments of the orbit (the other four are transposes)
         if (valid) {
@@ -396,7 +416,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
                     for (int b = 0; b < NB; ++b)
 #pragma unroll
                         for (int c = 0; c < NC; ++c) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoJ + b) * n + aoK + c);
-                    atomicAdd(Y + (size_t)(aoI + a) * n + aoL + d, (double)(w * s));
+                    atomicAdd(Y + (size_t)(aoI + a) * n + aoL + d, to_f64(w * s));
                 }
 #pragma unroll DUNR
             for (int b = 0; b < NB; ++b)
@@ -407,7 +427,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
                     for (int a = 0; a < NA; ++a)
 #pragma unroll
                         for (int c = 0; c < NC; ++c) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoI + a) * n + aoK + c);
-                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoL + d, (double)(w * s));
+                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoL + d, to_f64(w * s));
                 }
 #pragma unroll DUNR
             for (int a = 0; a < NA; ++a)
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
                     for (int b = 0; b < NB; ++b)
 #pragma unroll
                         for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoJ + b) * n + aoL + d);
-                    atomicAdd(Y + (size_t)(aoI + a) * n + aoK + c, (double)(w * s));
+                    atomicAdd(Y + (size_t)(aoI + a) * n + aoK + c, to_f64(w * s));
                 }
 #pragma unroll DUNR
             for (int b = 0; b < NB; ++b)
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
                     for (int a = 0; a < NA; ++a)
 #pragma unroll
                         for (int d = 0; d < ND; ++d) s += V[((a * NB + b) * NC + c) * ND + d] * __ldg(Dp + (size_t)(aoI + a) * n + aoL + d);
-                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoK + c, (double)(w * s));
+                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoK + c, to_f64(w * s));
                 }
         }
     }
@@ -442,11 +462,16 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
                 if (v != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, v);
             }
     }
-    // warp-aggregated count of the image quartets this launch evaluated
+    // warp-aggregated counts of the image quartets this launch evaluated and
+    // of their algorithmic flops (cnt[4])
     unsigned tot = nq;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        fl += __shfl_xor_sync(0xffffffffu, fl, o);
+    }
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);
+    if ((threadIdx.x & 31) == 0 && fl) atomicAdd(cnt + 4, fl);
 }
 
 // FP64 pass over the compact list of large quartets collected by the
@@ -462,13 +487,15 @@ __global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const in
     const unsigned total = min(*nbig, cap);
     const int n = pl.nbf;
     unsigned done = 0;
+    unsigned long long fl = 0;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int2 q = big[e];
         const SpiRec sb = pl.spi[q.x], sk = pl.spi[q.y];
         double V[NA * NB * NC * ND];
 #pragma unroll
         for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = 0.0;
-        quartet_block<LA, LB, LC, LD, double>(pl, sb, sk, V);
+        quartet_block<LA, LB, LC, LD, double>(pl, sb, sk, V, fl);
+        fl += flops::per_quartet(LA, LB, LC, LD);
         ++done;
         const double w = double(sb.w) * double(sk.w) * ((same && q.x == q.y) ? 0.5 : 1.0);
         const int aoI = pl.shells[sb.I].ao, aoJ = pl.shells[sb.J].ao, aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
@@ -542,8 +569,12 @@ __global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const in
     }
     unsigned tot = done;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        fl += __shfl_xor_sync(0xffffffffu, fl, o);
+    }
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);
+    if ((threadIdx.x & 31) == 0 && fl) atomicAdd(cnt + 4, fl);
 }
 
 // Structure factors of one class of unique shell pairs for a chunk of G.

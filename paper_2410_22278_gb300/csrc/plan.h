@@ -3,6 +3,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 #include <cmath>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -47,6 +48,7 @@ struct Workspace {
     size_t bytes = 0;
     // split-precision tensor-core exchange (mixed precision)
     int npad = 0, oz_slices = 0;
+    std::vector<int> chunk_slices;  // slices per G chunk (mixed exchange), <= oz_slices
     __nv_bfloat16 *Ms = nullptr, *Zs = nullptr, *Ds = nullptr, *Cs = nullptr;
     int *Mex = nullptr, *Zex = nullptr, *Dex = nullptr, *Cex = nullptr;
     // low-rank form of D (eigendecomposition on the device)
@@ -58,11 +60,17 @@ struct Workspace {
     bool lowrank = false;
     int rpos = 0, rneg = 0;
     double mma_flops = 0;  // BF16 MMA flops issued by the split-precision GEMMs of the last build
+    // tcgen05 form: TMA descriptors of the slice buffers (K-major rows, 128-byte
+    // swizzle, 64 x 128 boxes) and per-split FP64 partial sums of the exchange
+    bool tc = false;
+    CUtensorMap tm_Ms, tm_Ds, tm_Cs, tm_Zd, tm_Zl;
+    float2 *Kpart = nullptr;  // (hi, lo) float pairs
+    int kpart_splits = 0;
 };
 
 // CUDA events bracketing the phases of one build (see jk_build_times)
 struct PhaseTimer {
-    static constexpr int kPhases = 9;  // 0..6 as in jk_build_times, 7 tensor-core GEMMs, 8 their operand slicing
+    static constexpr int kPhases = 10;  // 0..6 as in jk_build_times, 7 tensor-core GEMMs, 8 their slicing, 9 FP64 list pass
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<int, int>>> marks;  // phase, (start event, end event)
     int next = 0;
@@ -90,6 +98,7 @@ struct Plan {
     std::vector<ClassRange> classes;
     std::vector<double> r1;    // [nr1][4]
     std::vector<double> gvec;  // [ng][4]
+    std::vector<double> gsize;  // [ng] bound on the exchange term of each G: (4 pi/V) e^{-G^2/4w^2}/G^2 s(G)^2
     std::vector<double> compf;
     std::vector<int> spair_class_off;  // shell pairs grouped by class: [JK_NCLASS_MAX+1]
     long long n_ord_shell_pairs = 0, n_ord_prim_pairs = 0, n_ord_local_pairs = 0;
@@ -130,7 +139,9 @@ int build_counts(Plan *p, long long *counts, int n);
 int autotune(Plan *p, const double *D, cudaStream_t st, const char *cache_path, int *chosen);
 int ozaki_begin(Plan *P, cudaStream_t st);
 int ozaki_prepare_lowrank(Plan *P, cudaStream_t st);
-int ozaki_exchange_chunk(Plan *P, int m2, cudaStream_t st);
+int ozaki_exchange_chunk(Plan *P, int m2, int S, cudaStream_t st);
+int ozaki_setup_tc(Plan *P);
+int ozaki_finish(Plan *P, cudaStream_t st);
 int energy_noalloc(const Plan *P, const double *D, const double *J, const double *K, double *e_coul, double *e_exch,
                    cudaStream_t st);
 

@@ -211,16 +211,17 @@ class Plan:
         _check(lib().jk_build_host(self._h, _dp(D), _dp(J) if J is not None else None, _dp(K) if K is not None else None,
                                    stream or None), "jk_build_host")
 
-    PHASES = ["prologue", "real_space", "recip_sfac", "recip_j", "recip_k", "epilogue", "total", "tensor_gemm", "tensor_slice"]
+    PHASES = ["prologue", "real_space", "recip_sfac", "recip_j", "recip_k", "epilogue", "total", "tensor_gemm", "tensor_slice",
+              "real_fp64_list"]
 
     def build_times(self):
         """{phase: (ms, launches)} of the most recent build (device events),
         plus "mma_flops": BF16 MMA flops issued by the tensor-core GEMMs."""
-        ms = (ctypes.c_double * 10)()
-        nl = (ctypes.c_int * 10)()
-        _check(lib().jk_build_times(self._h, ms, nl, 10), "jk_build_times")
+        ms = (ctypes.c_double * 11)()
+        nl = (ctypes.c_int * 11)()
+        _check(lib().jk_build_times(self._h, ms, nl, 11), "jk_build_times")
         out = {p: (ms[i], nl[i]) for i, p in enumerate(self.PHASES)}
-        out["mma_flops"] = (ms[9], 0)
+        out["mma_flops"] = (ms[10], 0)
         return out
 
     def autotune(self, D_ptr: int, stream: int = 0, cache_path: str = None):
@@ -235,6 +236,12 @@ class Plan:
         c = (ctypes.c_longlong * 4)()
         _check(lib().jk_build_counts(self._h, c, 4), "jk_build_counts")
         return int(c[0]), int(c[1])
+
+    def real_space_flops(self):
+        """(FP64, FP32) algorithmic flops of the real-space evaluation in the most recent build."""
+        c = (ctypes.c_longlong * 6)()
+        _check(lib().jk_build_counts(self._h, c, 6), "jk_build_counts")
+        return int(c[4]), int(c[5])
 
     def energy(self, D_ptr: int, J_ptr: int, K_ptr: int, stream: int = 0):
         ej, ek = ctypes.c_double(), ctypes.c_double()
