@@ -99,24 +99,40 @@ __global__ void k_final(int n, const double *__restrict__ f, const double *__res
 }
 
 template <int LA, int LB>
-static void sfac_go(const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, double *M, cudaStream_t st)
+static void sfac_go(const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, const double *gtab, double *M,
+                    cudaStream_t st)
 {
     const long long nt = (long long)(sp1 - sp0) * gcur;
     if (nt <= 0) return;
-    k_sfac<LA, LB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(pl, sp0, sp1, gv, g0, gcur, M);
+    k_sfac<LA, LB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(pl, sp0, sp1, gv, g0, gcur, gtab, M);
 }
 
-void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, double *M, cudaStream_t st)
+void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, const double *gtab, double *M,
+                 cudaStream_t st)
 {
     switch (cls) {
-    case 0: sfac_go<0, 0>(pl, sp0, sp1, gv, g0, gcur, M, st); break;
-    case 1: sfac_go<1, 0>(pl, sp0, sp1, gv, g0, gcur, M, st); break;
-    case 2: sfac_go<1, 1>(pl, sp0, sp1, gv, g0, gcur, M, st); break;
-    case 3: sfac_go<2, 0>(pl, sp0, sp1, gv, g0, gcur, M, st); break;
-    case 4: sfac_go<2, 1>(pl, sp0, sp1, gv, g0, gcur, M, st); break;
-    case 5: sfac_go<2, 2>(pl, sp0, sp1, gv, g0, gcur, M, st); break;
+    case 0: sfac_go<0, 0>(pl, sp0, sp1, gv, g0, gcur, gtab, M, st); break;
+    case 1: sfac_go<1, 0>(pl, sp0, sp1, gv, g0, gcur, gtab, M, st); break;
+    case 2: sfac_go<1, 1>(pl, sp0, sp1, gv, g0, gcur, gtab, M, st); break;
+    case 3: sfac_go<2, 0>(pl, sp0, sp1, gv, g0, gcur, gtab, M, st); break;
+    case 4: sfac_go<2, 1>(pl, sp0, sp1, gv, g0, gcur, gtab, M, st); break;
+    case 5: sfac_go<2, 2>(pl, sp0, sp1, gv, g0, gcur, gtab, M, st); break;
     default: break;
     }
+}
+
+// (pi/p)^{3/2} e^{-G^2/4p} for every distinct pair exponent p and every G of
+// a chunk, laid out [p][g] (consecutive threads of the structure-factor
+// kernel read consecutive g)
+__global__ void k_gauss_table(int npv, const double *__restrict__ pv, const double *__restrict__ gv, int g0, int gcur,
+                              double *__restrict__ tab)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)npv * gcur) return;
+    const int ip = (int)(e / gcur), gi = (int)(e % gcur);
+    const double *g = gv + 4 * (size_t)(g0 + gi);
+    const double G2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2], p = pv[ip];
+    tab[e] = (kPi / p) * sqrt(kPi / p) * exp(-G2 / (4.0 * p));
 }
 
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
@@ -132,7 +148,7 @@ int compute_overlap_raw(Plan *P, cudaStream_t st)
 {
     PlanDev pl = P->dev();
     for (int c = 0; c < JK_NCLASS_MAX; ++c)
-        launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_g0, 0, 1, P->ws.M, st);
+        launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_g0, 0, 1, P->d_gtab0, P->ws.M, st);
     cudaMemcpyAsync(P->d_S, P->ws.M, sizeof(double) * P->nbf * P->nbf, cudaMemcpyDeviceToDevice, st);
     return cuda_check("overlap");
 }
@@ -271,8 +287,12 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
         const int gcur = std::min(w.gc, ng - g0);
         ev = tm.start(2);
         int nsf = 0;
+        {
+            const long long ne = (long long)P->pvals.size() * gcur;
+            k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, w.gtab);
+        }
         for (int c = 0; c < JK_NCLASS_MAX; ++c) {
-            launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.M, st);
+            launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, w.M, st);
             nsf += P->spair_class_off[c + 1] > P->spair_class_off[c];
         }
         if ((rc = cuda_check("structure factors"))) return rc;

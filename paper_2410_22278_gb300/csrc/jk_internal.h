@@ -39,6 +39,8 @@ struct SpiRec {      // one unique shell-pair image
     double Q;        // Schwarz estimate (Eq. pbc_eri_cauchy_schwarz_cutoff_definition, summed over primitives)
     float Pc[3];     // centre of the image's largest primitive pair
     float ext;       // max |P_i - Pc| over its primitive pairs
+    float S;         // sum over its primitive pairs of |K| p^{-5/4} (quartet-level real-space bound)
+    float pmin;      // smallest pair exponent p among them
 };
 
 struct PpiRec {      // one local primitive pair
@@ -80,6 +82,8 @@ struct PlanDev {
     const double *gvec;          // [ng][4]: Gx, Gy, Gz, sqrt(8 pi w(G) / V)
     int ng;
     const double *compf;         // Cartesian component factor of each AO
+    const int *ppi_pidx;         // index of each primitive pair's exponent p among the distinct ones
+    const double2 *phase;        // (cos, sin)(2 pi k / 1024), k = 0..1023
     double L[9];                 // lattice rows a, b, c
     double Finv[9];              // fractional coordinates f = Finv * r
     float Lf[9], Finvf[9];       // the same in single precision (no conversions in FP32 kernels)
@@ -88,4 +92,6 @@ struct PlanDev {
     double ewald_R;              // delta_Ewald-R as given
     float log_ewald_R;           // ln of the per-term threshold used inside the real-space sums
     double volume;
+    float hplane[3];             // spacing of the lattice planes of each fractional coordinate
+    int orth;                    // lattice vectors mutually orthogonal: rounding f gives the minimum image
 };

@@ -85,14 +85,22 @@ __device__ __forceinline__ void seeds(double x2, double alpha, double aw, double
 // Single precision unless c_w is close to 1 (the integration interval
 // [c_w, 1] is short and the table branch would lose bits), where the seed is
 // formed in double and rounded once.
+// The FP64 branch sits in its own non-inlined function so that it stays a
+// branch: inlined, the compiler may predicate its FP64 instructions into the
+// float path, where they would occupy GB300's slow FP64 pipe on every call.
+template <int L>
+__device__ __noinline__ void seeds_fp64_rounded(float x2, float alpha, float aw, float cw, const PlanDev &pl, float *s)
+{
+    double sd[L + 1];
+    seeds<L>((double)x2, (double)alpha, (double)aw, (double)cw, pl, sd);
+#pragma unroll
+    for (int m = 0; m <= L; ++m) s[m] = (float)sd[m];
+}
 template <int L>
 __device__ __forceinline__ void seeds(float x2, float alpha, float aw, float cw, const PlanDev &pl, float *s)
 {
     if (cw > 0.85f) {
-        double sd[L + 1];
-        seeds<L>((double)x2, (double)alpha, (double)aw, (double)cw, pl, sd);
-#pragma unroll
-        for (int m = 0; m <= L; ++m) s[m] = (float)sd[m];
+        seeds_fp64_rounded<L>(x2, alpha, aw, cw, pl, s);
         return;
     }
     float G[L + 1];
@@ -188,10 +196,12 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
             if (!(lg > 0.0f)) continue;
             float r = sqrtf(lg / awf);
-            r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
-            r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
-            // the Gaussian bound is derived for s functions; widen for L > 0
-            r += L > 0 ? 0.5f + 0.25f * L : 0.0f;
+            if (L > 0) {
+                r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+                r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+                // the Gaussian bound is derived for s functions; widen for L > 0
+                r += 0.5f + 0.25f * L;
+            }
             const float r2 = r * r;
             PairT<T> y;
             load_pair(pl, sk.pp0 + j, yf, y);
@@ -294,6 +304,52 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
     }
 }
 
+// Quartet-level real-space bound: false only if no primitive quartet of the
+// pair of images can have an image term inside its screening sphere, so the
+// quartet contributes nothing and its primitive loop can be skipped.  Every
+// primitive prefactor 2 pi^{5/2} |K_i K_j| / (p q sqrt(p+q)) is at most
+// 2 pi^{5/2} 2^{-1/2} |K_i| p^{-5/4} |K_j| q^{-5/4} (p + q >= 2 sqrt(pq)), so
+// sum-free B0 = 2 pi^{5/2} 2^{-1/2} S_bra S_ket bounds each of them; the
+// screening radius grows with the prefactor and, through both terms of its
+// fixed-point form, shrinks as alpha_w grows, so the radius from (B0, the
+// smallest alpha_w) dominates every primitive radius.  The distance is a
+// lower bound on |P_i - Q_j - R1| over all lattice vectors R1: the distance
+// from the image centres' difference to the lattice (exact minimum image for
+// orthogonal cells, else the largest plane-spacing projection) less both
+// extents.
+template <int L>
+__device__ __forceinline__ bool quartet_reaches(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk)
+{
+    const float B0 = 24.7394241f * sb.S * sk.S * 1.001f;  // 2 pi^{5/2} / sqrt 2
+    const float lg = __logf(B0) - pl.log_ewald_R;
+    if (!(lg > 0.0f)) return false;
+    const float aw = 1.0f / (1.0f / sb.pmin + 1.0f / sk.pmin + pl.inv_omega2f);
+    float r = sqrtf(lg / aw);
+    if (L > 0) {
+        r = sqrtf((lg + L * __logf(1.0f + 2.0f * aw * r)) / aw);
+        r = sqrtf((lg + L * __logf(1.0f + 2.0f * aw * r)) / aw);
+    }
+    r = r * 1.0001f + (L > 0 ? 0.5f + 0.25f * L : 0.0f) + sb.ext + sk.ext + 1e-3f;
+    const float X[3] = {sb.Pc[0] - sk.Pc[0], sb.Pc[1] - sk.Pc[1], sb.Pc[2] - sk.Pc[2]};
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[a] = pl.Finvf[3 * a] * X[0] + pl.Finvf[3 * a + 1] * X[1] + pl.Finvf[3 * a + 2] * X[2];
+        f[a] -= rintf(f[a]);
+    }
+    float d2;
+    if (pl.orth) {
+        float Y[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Y[a] = f[0] * pl.Lf[a] + f[1] * pl.Lf[3 + a] + f[2] * pl.Lf[6 + a];
+        d2 = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+    } else {
+        const float d = fmaxf(fmaxf(pl.hplane[0] * fabsf(f[0]), pl.hplane[1] * fabsf(f[1])), pl.hplane[2] * fabsf(f[2]));
+        d2 = d * d;
+    }
+    return d2 < r * r;
+}
+
 // Size estimate of the real-space block of a pair of images, for the
 // precision switch (not for screening): the sum over primitive quartets of
 // the Gaussian bound behind Eq. pbc_eri_real_cutoff_definition,
@@ -320,6 +376,22 @@ __device__ __forceinline__ float quartet_estimate(const PlanDev &pl, const SpiRe
         }
     }
     return est;
+}
+
+// O(1) upper bound of quartet_estimate (same distance d; each primitive term
+// bounded as in quartet_reaches, with 1 - c_w <= 1 and the smallest alpha_w):
+// quartets below tau by this bound need no per-primitive estimate.
+__device__ __forceinline__ float quartet_estimate_bound(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk)
+{
+    float X[3] = {sb.Pc[0] - sk.Pc[0], sb.Pc[1] - sk.Pc[1], sb.Pc[2] - sk.Pc[2]};
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = rintf(pl.Finvf[3 * a] * X[0] + pl.Finvf[3 * a + 1] * X[1] + pl.Finvf[3 * a + 2] * X[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) X[a] -= f[0] * pl.Lf[a] + f[1] * pl.Lf[3 + a] + f[2] * pl.Lf[6 + a];
+    const float d = fmaxf(0.0f, sqrtf(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
+    const float aw = 1.0f / (1.0f / sb.pmin + 1.0f / sk.pmin + pl.inv_omega2f);
+    return 24.7394241f * 1.001f * sb.S * sk.S * __expf(-aw * d * d);
 }
 
 // mode 0: every quartet in this kernel's precision.  mode 2 (mixed
@@ -360,10 +432,12 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
     for (int kt = kbeg; kt < kend; ++kt) {
         const SpiRec sk = pl.spi[kt];
         bool valid = act && (!same || kt >= bra);
+        valid = valid && quartet_reaches<LA + LB + LC + LD>(pl, sb, sk);
+        if (!__any_sync(0xffffffffu, valid)) continue;  // no lane of the warp has work for this ket
         if (valid && mode) {
             float dm = fmaxf(fmaxf((float)dIJ, (float)dmax[sk.I * nsh + sk.J]), fmaxf((float)dmax[sb.J * nsh + sk.I], (float)dmax[sb.I * nsh + sk.I]));
             dm = fmaxf(dm, fmaxf((float)dmax[sb.J * nsh + sk.J], (float)dmax[sb.I * nsh + sk.J]));
-            const float est = quartet_estimate(pl, sb, sk) * dm;
+            const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
             if (est >= tauf) {
                 const unsigned slot = atomicAdd(nbig, 1u);
                 if (slot < cap) {
@@ -577,12 +651,32 @@ __global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const in
     if ((threadIdx.x & 31) == 0 && fl) atomicAdd(cnt + 4, fl);
 }
 
+// sin and cos of a phase in FP64 by table and angle addition: theta =
+// k (2 pi / 1024) + e with k = rint(theta 1024 / 2 pi), reduced with the
+// step split in two (a 32-bit head, so k * head is exact for |k| < 2^21, and
+// the remainder); |e| <= pi/1024 + rounding, where seven-term sine and
+// eight-term cosine Taylor series are exact to double rounding; then
+// sin(a + e) = sin a cos e + cos a sin e, cos(a + e) = cos a cos e - sin a sin e
+// with (cos a, sin a) from the 1024-entry table.
+__device__ __forceinline__ void phase_sincos(double th, const double2 *__restrict__ tab, double &s, double &c)
+{
+    const double kd = rint(th * 162.97466172610083);  // 1024 / (2 pi)
+    double e = fma(-kd, 0.006135923151305178, th);  // 2 pi / 1024, head
+    e = fma(-kd, 2.3738673853539813e-13, e);        // tail
+    const double2 t = __ldg(tab + ((int)kd & 1023));
+    const double e2 = e * e;
+    const double se = e * (1.0 + e2 * (-1.0 / 6.0 + e2 * (1.0 / 120.0 - e2 * (1.0 / 5040.0))));
+    const double ce = 1.0 + e2 * (-0.5 + e2 * (1.0 / 24.0 + e2 * (-1.0 / 720.0 + e2 * (1.0 / 40320.0))));
+    s = t.y * ce + t.x * se;
+    c = t.x * ce - t.y * se;
+}
+
 // Structure factors of one class of unique shell pairs for a chunk of G.
 // Thread (shell pair, g) with g fastest.  M layout: [2*gcur][n][n], part 0
 // real, part 1 imaginary, both scaled by sqrt(8 pi w(G)/V) (gv[4g+3]).
 template <int LA, int LB>
 __global__ void __launch_bounds__(128) k_sfac(PlanDev pl, int sp0, int sp1, const double *__restrict__ gv, int g0, int gcur,
-                                              double *__restrict__ M)
+                                              const double *__restrict__ gtab, double *__restrict__ M)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NT = LA + LB + 1;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -591,7 +685,6 @@ __global__ void __launch_bounds__(128) k_sfac(PlanDev pl, int sp0, int sp1, cons
     if (sp >= sp1) return;
     const SpairRec rec = pl.spair[sp];
     const double Gx = gv[4 * (g0 + gi)], Gy = gv[4 * (g0 + gi) + 1], Gz = gv[4 * (g0 + gi) + 2], sw = gv[4 * (g0 + gi) + 3];
-    const double G2 = Gx * Gx + Gy * Gy + Gz * Gz;
     const double Gv[3] = {Gx, Gy, Gz};
     double re[NA * NB], im[NA * NB];
 #pragma unroll
@@ -602,9 +695,10 @@ __global__ void __launch_bounds__(128) k_sfac(PlanDev pl, int sp0, int sp1, cons
         const bool rzero = si.n[0] == 0 && si.n[1] == 0 && si.n[2] == 0;
         for (int pp = 0; pp < si.npp; ++pp) {
             const PpiRec x = pl.ppi[si.pp0 + pp];
-            const double amp = x.K * (kPi / x.p) * sqrt(kPi / x.p) * exp(-G2 / (4.0 * x.p));
+            // K (pi/p)^{3/2} e^{-G^2/4p}, the Gaussian factor from the chunk's table
+            const double amp = x.K * __ldg(gtab + (size_t)__ldg(pl.ppi_pidx + si.pp0 + pp) * gcur + gi);
             double sn, cs;
-            sincos(Gx * x.P[0] + Gy * x.P[1] + Gz * x.P[2], &sn, &cs);
+            phase_sincos(Gx * x.P[0] + Gy * x.P[1] + Gz * x.P[2], pl.phase, sn, cs);
             const double pr = amp * cs, pim = -amp * sn;  // amp * e^{-iG.P}
             // per-axis polynomials h[ax][i][j] = sum_t E^{ij}_t (-i G)^t  (complex)
             double hr[3][(LA + 1) * (LB + 1)], hi[3][(LA + 1) * (LB + 1)];

@@ -24,6 +24,7 @@ struct RealLaunch {
     cudaStream_t st;
 };
 
-void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, double *M, cudaStream_t st);
+void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv, int g0, int gcur, const double *gtab, double *M,
+                 cudaStream_t st);
 
 }  // namespace jk

@@ -216,6 +216,8 @@ PlanDev Plan::dev() const
     d.gvec = d_gvec;
     d.ng = (int)(gvec.size() / 4);
     d.compf = d_compf;
+    d.ppi_pidx = d_ppi_pidx;
+    d.phase = d_phase;
     memcpy(d.L, L, sizeof L);
     memcpy(d.Finv, Finv, sizeof Finv);
     for (int i = 0; i < 9; ++i) {
@@ -231,6 +233,16 @@ PlanDev Plan::dev() const
     // (plus an angular-momentum margin in the kernels).
     d.log_ewald_R = (float)std::log(cut.ewald_R * 1e-1);
     d.volume = volume;
+    for (int a = 0; a < 3; ++a)
+        d.hplane[a] = (float)(1.0 / std::sqrt(Finv[3 * a] * Finv[3 * a] + Finv[3 * a + 1] * Finv[3 * a + 1] + Finv[3 * a + 2] * Finv[3 * a + 2]));
+    d.orth = 1;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) {
+            const double dot = L[3 * a] * L[3 * b] + L[3 * a + 1] * L[3 * b + 1] + L[3 * a + 2] * L[3 * b + 2];
+            const double na = std::sqrt(L[3 * a] * L[3 * a] + L[3 * a + 1] * L[3 * a + 1] + L[3 * a + 2] * L[3 * a + 2]);
+            const double nb = std::sqrt(L[3 * b] * L[3 * b] + L[3 * b + 1] * L[3 * b + 1] + L[3 * b + 2] * L[3 * b + 2]);
+            if (std::fabs(dot) > 1e-12 * na * nb) d.orth = 0;
+        }
     return d;
 }
 
@@ -290,7 +302,7 @@ static int alloc_ws(Plan *P)
         bytes += std::max<size_t>(count, 1) * sizeof(double);
         return true;
     };
-    bool ok = al(&w.Dp, n2) && al(&w.X, n2) && al(&w.Y, n2) && al(&w.JLR, n2) && al(&w.KLR, n2) && al(&w.T1, n2) &&
+    bool ok = al(&w.gtab, std::max<size_t>(1, P->pvals.size()) * (size_t)gc) && al(&w.Dp, n2) && al(&w.X, n2) && al(&w.Y, n2) && al(&w.JLR, n2) && al(&w.KLR, n2) && al(&w.T1, n2) &&
               al(&w.T2, n2) && al(&w.M, 2 * (size_t)gc * n2) && al(&w.Z, 2 * (size_t)gc * n2) && al(&w.rho, 2 * (size_t)gc) &&
               al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16) && (!mixed || al((double **)&w.Dpf, (n2 + 1) / 2)) &&
               (!mixed || al((double **)&w.dmaxf, ((size_t)P->nshell * P->nshell + 1) / 2));
@@ -506,26 +518,49 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                 sr.Q = Q;
                 for (int k = 0; k < 3; ++k) sr.Pc[k] = (float)pv[0].P[k];
                 sr.ext = 0.f;
+                double Ssum = 0, pmin = 1e300;
                 for (auto &x : pv) {
                     double d2 = 0;
                     for (int k = 0; k < 3; ++k) d2 += (x.P[k] - pv[0].P[k]) * (x.P[k] - pv[0].P[k]);
                     sr.ext = std::max(sr.ext, (float)std::sqrt(d2));
+                    Ssum += std::fabs(x.K) * std::pow(x.p, -1.25);
+                    pmin = std::min(pmin, x.p);
                 }
+                // rounded up and down respectively, so the float bound stays a bound
+                sr.S = (float)(Ssum * (1.0 + 1e-6));
+                sr.pmin = (float)(pmin * (1.0 - 1e-6));
                 spis.push_back(sr);
                 spi_ppis.push_back(std::move(pv));
             }
         }
     }
-    // ---- sort images by class, then descending Schwarz estimate (Section 3.1)
+    // ---- sort images by class, primitive count and position (Section 3.1 sorts by the Schwarz estimate)
     std::vector<int> order(spis.size());
     std::iota(order.begin(), order.end(), 0);
     auto cls_of = [&](const SpiRec &s) { return pair_class(P->shells[s.I].l, P->shells[s.J].l); };
     // class, then primitive-pair count (lanes of a warp do similar work),
-    // then descending Schwarz estimate (Section 3.1's prefactor order)
+    // then position: Morton order of the image centre in the cell, so that
+    // the 32 bras of a warp, and consecutive kets, lie close together and the
+    // quartet-level real-space bound rejects the same kets for a whole warp
+    std::vector<unsigned long long> morton(spis.size());
+    for (size_t i = 0; i < spis.size(); ++i) {
+        unsigned long long code = 0;
+        unsigned q[3];
+        for (int a = 0; a < 3; ++a) {
+            double f = 0;
+            for (int b = 0; b < 3; ++b) f += P->Finv[3 * a + b] * spis[i].Pc[b];
+            f -= std::floor(f);
+            q[a] = std::min(1023u, (unsigned)(f * 1024.0));
+        }
+        for (int bit = 9; bit >= 0; --bit)
+            for (int a = 0; a < 3; ++a) code = (code << 1) | ((q[a] >> bit) & 1u);
+        morton[i] = code;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         int ca = cls_of(spis[a]), cb = cls_of(spis[b]);
         if (ca != cb) return ca < cb;
         if (spis[a].npp != spis[b].npp) return spis[a].npp > spis[b].npp;
+        if (morton[a] != morton[b]) return morton[a] < morton[b];
         return spis[a].Q > spis[b].Q;
     });
     for (int idx : order) {
@@ -751,6 +786,29 @@ int finish_plan_device(Plan *P)
     if ((rc = upload(tab, &P->d_boys, b)) || (rc = upload(tabf, &P->d_boys_f, b))) return rc;
     std::vector<double> g0 = {0.0, 0.0, 0.0, 1.0};
     if ((rc = upload(g0, &P->d_g0, b))) return rc;
+    {
+        // distinct pair exponents (exact equality) and each primitive pair's index
+        std::map<double, int> pid;
+        for (auto &x : P->ppi) pid.emplace(x.p, 0);
+        P->pvals.clear();
+        for (auto &kv : pid) {
+            kv.second = (int)P->pvals.size();
+            P->pvals.push_back(kv.first);
+        }
+        P->ppi_pidx.resize(P->ppi.size());
+        for (size_t i = 0; i < P->ppi.size(); ++i) P->ppi_pidx[i] = pid[P->ppi[i].p];
+        std::vector<double> gt0(P->pvals.size());
+        for (size_t i = 0; i < gt0.size(); ++i) gt0[i] = std::pow(kPi / P->pvals[i], 1.5);
+        // phase table, rounded from extended precision
+        std::vector<double2> ph(1024);
+        for (int k = 0; k < 1024; ++k) {
+            const long double t = 2.0L * 3.141592653589793238462643383279502884L * k / 1024.0L;
+            ph[k] = make_double2((double)std::cos(t), (double)std::sin(t));
+        }
+        if ((rc = upload(P->pvals, &P->d_pvals, b)) || (rc = upload(P->ppi_pidx, &P->d_ppi_pidx, b)) || (rc = upload(gt0, &P->d_gtab0, b)) ||
+            (rc = upload(ph, &P->d_phase, b)))
+            return rc;
+    }
     std::vector<double> zeros((size_t)P->nbf * P->nbf, 0.0);
     if ((rc = upload(zeros, &P->d_S, b))) return rc;
     if ((rc = alloc_ws(P))) return rc;
@@ -765,7 +823,7 @@ void destroy_plan(Plan *P)
     if (!P) return;
     cudaSetDevice(P->device);
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
-                    P->d_g0, P->d_compf, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
+                    P->d_g0, P->d_compf, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->ws.gtab, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
                     P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
                     P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
                     P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};

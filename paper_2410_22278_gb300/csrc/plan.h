@@ -45,6 +45,7 @@ struct Workspace {
     unsigned *nbig = nullptr;           // [0] list length, [1] overflow count (accumulated over a build)
     unsigned cap = 0;
     int gc = 0;               // G vectors per chunk
+    double *gtab = nullptr;   // [distinct p][gc]: (pi/p)^{3/2} e^{-G^2/4p} of the current G chunk
     size_t bytes = 0;
     // split-precision tensor-core exchange (mixed precision)
     int npad = 0, oz_slices = 0;
@@ -119,6 +120,13 @@ struct Plan {
     double *d_r1 = nullptr;
     double *d_gvec = nullptr;
     double *d_g0 = nullptr;  // one G = 0 entry with unit weight (overlap)
+    // structure-factor tables: distinct pair exponents, the exponent index of
+    // each primitive pair, (cos, sin)(2 pi k / 1024), and (pi/p)^{3/2} (G = 0)
+    std::vector<double> pvals;
+    std::vector<int> ppi_pidx;
+    double *d_pvals = nullptr, *d_gtab0 = nullptr;
+    int *d_ppi_pidx = nullptr;
+    double2 *d_phase = nullptr;
     double *d_compf = nullptr;
     double *d_S = nullptr;  // raw-component overlap over the pair list
     size_t device_bytes = 0;
