@@ -70,6 +70,8 @@ struct PlanDev {
     int nspi, nppi, nspair;
     const ShellRec *shells;
     const SpiRec *spi;
+    const float4 *kblk;          // images 32k .. 32k+31: bounding sphere (centre, radius including extents)
+    const float2 *kblk2;         // the same images: largest S, smallest pair exponent
     const PpiRec *ppi;
     const SpairRec *spair;
     const int *spi_order;        // spi indices grouped by shell pair (for the reciprocal build)

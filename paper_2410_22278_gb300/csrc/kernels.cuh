@@ -85,24 +85,14 @@ __device__ __forceinline__ void seeds(double x2, double alpha, double aw, double
 // Single precision unless c_w is close to 1 (the integration interval
 // [c_w, 1] is short and the table branch would lose bits), where the seed is
 // formed in double and rounded once.
-// The FP64 branch sits in its own non-inlined function so that it stays a
-// branch: inlined, the compiler may predicate its FP64 instructions into the
-// float path, where they would occupy GB300's slow FP64 pipe on every call.
-template <int L>
-__device__ __noinline__ void seeds_fp64_rounded(float x2, float alpha, float aw, float cw, const PlanDev &pl, float *s)
-{
-    double sd[L + 1];
-    seeds<L>((double)x2, (double)alpha, (double)aw, (double)cw, pl, sd);
-#pragma unroll
-    for (int m = 0; m <= L; ++m) s[m] = (float)sd[m];
-}
+// Single precision throughout.  The mixed path sends every quartet whose
+// largest c_w exceeds 0.85 (the integration interval [c_w, 1] is short and
+// the table branch would lose bits) to the FP64 list instead (k_real, mode
+// 2), so this form never sees such a seed.
 template <int L>
 __device__ __forceinline__ void seeds(float x2, float alpha, float aw, float cw, const PlanDev &pl, float *s)
 {
-    if (cw > 0.85f) {
-        seeds_fp64_rounded<L>(x2, alpha, aw, cw, pl, s);
-        return;
-    }
+    (void)aw;
     float G[L + 1];
     boys_attenuated<L, float>(alpha * x2, cw, pl.boys_f, G);
     float f = 1.0f;
@@ -193,6 +183,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             const float awf = 1.0f / (ipf + iqf + iw2);
             const float cwf = sqrtf(awf * (ipf + iqf));
             const float preff = 34.986836655249725f * xf.K * yf.K * ipf * iqf * rsqrtf(xf.p + yf.p);
+
             const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
             if (!(lg > 0.0f)) continue;
             float r = sqrtf(lg / awf);
@@ -318,19 +309,20 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
 // orthogonal cells, else the largest plane-spacing projection) less both
 // extents.
 template <int L>
-__device__ __forceinline__ bool quartet_reaches(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk)
+__device__ __forceinline__ bool reaches(const PlanDev &pl, const SpiRec &sb, float kx, float ky, float kz, float kext, float kS,
+                                        float kpmin)
 {
-    const float B0 = 24.7394241f * sb.S * sk.S * 1.001f;  // 2 pi^{5/2} / sqrt 2
+    const float B0 = 24.7394241f * sb.S * kS * 1.001f;  // 2 pi^{5/2} / sqrt 2
     const float lg = __logf(B0) - pl.log_ewald_R;
     if (!(lg > 0.0f)) return false;
-    const float aw = 1.0f / (1.0f / sb.pmin + 1.0f / sk.pmin + pl.inv_omega2f);
+    const float aw = 1.0f / (1.0f / sb.pmin + 1.0f / kpmin + pl.inv_omega2f);
     float r = sqrtf(lg / aw);
     if (L > 0) {
         r = sqrtf((lg + L * __logf(1.0f + 2.0f * aw * r)) / aw);
         r = sqrtf((lg + L * __logf(1.0f + 2.0f * aw * r)) / aw);
     }
-    r = r * 1.0001f + (L > 0 ? 0.5f + 0.25f * L : 0.0f) + sb.ext + sk.ext + 1e-3f;
-    const float X[3] = {sb.Pc[0] - sk.Pc[0], sb.Pc[1] - sk.Pc[1], sb.Pc[2] - sk.Pc[2]};
+    r = r * 1.0001f + (L > 0 ? 0.5f + 0.25f * L : 0.0f) + sb.ext + kext + 1e-3f;
+    const float X[3] = {sb.Pc[0] - kx, sb.Pc[1] - ky, sb.Pc[2] - kz};
     float f[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -348,6 +340,23 @@ __device__ __forceinline__ bool quartet_reaches(const PlanDev &pl, const SpiRec 
         d2 = d * d;
     }
     return d2 < r * r;
+}
+template <int L>
+__device__ __forceinline__ bool quartet_reaches(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk)
+{
+    return reaches<L>(pl, sb, sk.Pc[0], sk.Pc[1], sk.Pc[2], sk.ext, sk.S, sk.pmin);
+}
+// The same bound for a block of 32 consecutive ket images: the block's
+// sphere contains every member's centre shifted next to the first member
+// (the lattice distance to a bra does not change under that shift) plus its
+// extent, and its S and exponent bound every member's, so a bra that cannot
+// reach the block cannot reach any of its images.
+template <int L>
+__device__ __forceinline__ bool block_reaches(const PlanDev &pl, const SpiRec &sb, int blk)
+{
+    const float4 c = __ldg(pl.kblk + blk);
+    const float2 t = __ldg(pl.kblk2 + blk);
+    return reaches<L>(pl, sb, c.x, c.y, c.z, c.w, t.x, t.y);
 }
 
 // Size estimate of the real-space block of a pair of images, for the
@@ -376,6 +385,14 @@ __device__ __forceinline__ float quartet_estimate(const PlanDev &pl, const SpiRe
         }
     }
     return est;
+}
+
+// max |D'| over the six shell blocks an image quartet (ij|kl) digests into
+// (FP32 shell-block maxima; exact, so every caller gets the same value)
+__device__ __forceinline__ float quartet_dmax(const float *__restrict__ dm, int nsh, const SpiRec &sb, const SpiRec &sk)
+{
+    const float a = fmaxf(fmaxf(dm[sb.I * nsh + sb.J], dm[sk.I * nsh + sk.J]), fmaxf(dm[sb.J * nsh + sk.I], dm[sb.I * nsh + sk.I]));
+    return fmaxf(a, fmaxf(dm[sb.J * nsh + sk.J], dm[sb.I * nsh + sk.J]));
 }
 
 // O(1) upper bound of quartet_estimate (same distance d; each primitive term
@@ -425,20 +442,30 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
     for (int a = 0; a < NA; ++a)
 #pragma unroll
         for (int b = 0; b < NB; ++b) Dij[a * NB + b] = __ldg(Dp + (size_t)(aoI + a) * n + aoJ + b);
-    const T dIJ = mode ? dmax[sb.I * nsh + sb.J] : T(0);
     const float tauf = (float)tau;
     unsigned nq = 0;
     unsigned long long fl = 0;  // algorithmic flops (flops.h)
     for (int kt = kbeg; kt < kend; ++kt) {
+        // one bound per block of 32 kets for the whole warp first
+        if (kt == kbeg || (kt & 31) == 0) {
+            if (!__any_sync(0xffffffffu, act && block_reaches<LA + LB + LC + LD>(pl, sb, kt >> 5))) {
+                kt = min(kend, ((kt >> 5) + 1) << 5) - 1;
+                continue;
+            }
+        }
         const SpiRec sk = pl.spi[kt];
         bool valid = act && (!same || kt >= bra);
         valid = valid && quartet_reaches<LA + LB + LC + LD>(pl, sb, sk);
         if (!__any_sync(0xffffffffu, valid)) continue;  // no lane of the warp has work for this ket
-        if (valid && mode) {
-            float dm = fmaxf(fmaxf((float)dIJ, (float)dmax[sk.I * nsh + sk.J]), fmaxf((float)dmax[sb.J * nsh + sk.I], (float)dmax[sb.I * nsh + sk.I]));
-            dm = fmaxf(dm, fmaxf((float)dmax[sb.J * nsh + sk.J], (float)dmax[sb.I * nsh + sk.J]));
+        // mixed precision (mode 2, FP32 kernel): a quartet whose size estimate
+        // reaches tau, or whose [c_w, 1] interval is short, is listed for the
+        // FP64 pass instead of being evaluated here
+        if (sizeof(T) == 4 && valid && mode) {
+            const float dm = quartet_dmax(reinterpret_cast<const float *>(dmax), nsh, sb, sk);
             const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
-            if (est >= tauf) {
+            // largest c_w^2 = (1/p + 1/q) / (1/p + 1/q + 1/w^2) over the quartet's primitives
+            const float ipq = 1.0f / sb.pmin + 1.0f / sk.pmin;
+            if (est >= tauf || ipq > 0.7225f * (ipq + pl.inv_omega2f)) {
                 const unsigned slot = atomicAdd(nbig, 1u);
                 if (slot < cap) {
                     big[slot] = make_int2(bra, kt);

@@ -204,6 +204,8 @@ PlanDev Plan::dev() const
     d.nspair = (int)spair.size();
     d.shells = d_shells;
     d.spi = d_spi;
+    d.kblk = d_kblk;
+    d.kblk2 = d_kblk2;
     d.ppi = d_ppi;
     d.spair = d_spair;
     d.spi_order = d_spi_order;
@@ -760,6 +762,40 @@ int finish_plan_device(Plan *P)
     if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
     int rc;
     size_t &b = P->device_bytes;
+    {
+        // bounding spheres of blocks of 32 consecutive images (in the kernels'
+        // ket order): members are moved next to the block's first image by the
+        // minimum image (the lattice distance to any bra is unchanged), then
+        // centre = mean, radius = max |Pc - centre| + ext
+        const int nsp = (int)P->spi.size(), nblk = (nsp + 31) / 32;
+        std::vector<float4> kb(std::max(nblk, 1));
+        std::vector<float2> kb2(std::max(nblk, 1));
+        for (int bl = 0; bl < nblk; ++bl) {
+            const int i0 = 32 * bl, i1 = std::min(nsp, i0 + 32);
+            std::vector<std::array<double, 3>> q;
+            double c[3] = {0, 0, 0}, smax = 0, pmin = 1e300;
+            for (int i = i0; i < i1; ++i) {
+                double d[3], f[3];
+                for (int k = 0; k < 3; ++k) d[k] = (double)P->spi[i].Pc[k] - (double)P->spi[i0].Pc[k];
+                for (int a = 0; a < 3; ++a) f[a] = std::rint(P->Finv[3 * a] * d[0] + P->Finv[3 * a + 1] * d[1] + P->Finv[3 * a + 2] * d[2]);
+                std::array<double, 3> x;
+                for (int k = 0; k < 3; ++k) x[k] = (double)P->spi[i0].Pc[k] + d[k] - (f[0] * P->L[k] + f[1] * P->L[3 + k] + f[2] * P->L[6 + k]);
+                q.push_back(x);
+                for (int k = 0; k < 3; ++k) c[k] += x[k] / (i1 - i0);
+                smax = std::max(smax, (double)P->spi[i].S);
+                pmin = std::min(pmin, (double)P->spi[i].pmin);
+            }
+            double rad = 0;
+            for (int i = i0; i < i1; ++i) {
+                const auto &x = q[i - i0];
+                const double r = std::sqrt((x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) + (x[2] - c[2]) * (x[2] - c[2]));
+                rad = std::max(rad, r + (double)P->spi[i].ext);
+            }
+            kb[bl] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)(rad * (1 + 1e-6) + 1e-4));
+            kb2[bl] = make_float2((float)smax, (float)pmin);
+        }
+        if ((rc = upload(kb, &P->d_kblk, b)) || (rc = upload(kb2, &P->d_kblk2, b))) return rc;
+    }
     if ((rc = upload(P->shells, &P->d_shells, b)) || (rc = upload(P->spi, &P->d_spi, b)) || (rc = upload(P->ppi, &P->d_ppi, b)) ||
         (rc = upload(P->spair, &P->d_spair, b)) || (rc = upload(P->spi_order, &P->d_spi_order, b)) ||
         (rc = upload(P->r1, &P->d_r1, b)) || (rc = upload(P->gvec, &P->d_gvec, b)) || (rc = upload(P->compf, &P->d_compf, b)))
@@ -823,7 +859,7 @@ void destroy_plan(Plan *P)
     if (!P) return;
     cudaSetDevice(P->device);
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
-                    P->d_g0, P->d_compf, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->ws.gtab, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
+                    P->d_g0, P->d_compf, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->ws.gtab, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
                     P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
                     P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
                     P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};

@@ -110,6 +110,8 @@ struct Plan {
     // device arrays
     ShellRec *d_shells = nullptr;
     SpiRec *d_spi = nullptr;
+    float4 *d_kblk = nullptr;  // per 32 consecutive images: bounding-sphere centre and radius (incl. extents)
+    float2 *d_kblk2 = nullptr; // per 32 consecutive images: largest S, smallest pair exponent
     PpiRec *d_ppi = nullptr;
     PpiF *d_ppf = nullptr;
     float *d_r1f = nullptr;
