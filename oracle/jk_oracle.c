@@ -1114,3 +1114,197 @@ void orc_jk_sample(const orc_basis *bs, const double *D, int bra_stride, int ng_
     free(Lall.v);
     free(off);
 }
+
+/* ------------------------------------------------------------------ */
+/* One-electron operators of the cell: kinetic energy and nuclear
+ * attraction (Sections 2.1 and 2.2 of the paper; the kinetic formula is in
+ * its Supporting Information).  Like the overlap, both are sums over the
+ * pair list of local integrals between mu at A and nu at B + R.          */
+
+/* 1-D overlap of (x-A)^i e^{-a(x-A)^2} and (x-B)^j e^{-b(x-B)^2} without the
+ * Gaussian factor exp(-ab/p (A-B)^2) (carried by K): binomial expansion
+ * about P and the Gaussian moments int u^n e^{-p u^2} du =
+ * Gamma((n+1)/2) / p^{(n+1)/2} for even n, 0 for odd n.                  */
+static double ov_1d(int i, int j, double A, double B, double P, double p)
+{
+    double s = 0;
+    for (int k = 0; k <= i; k++)
+        for (int l = 0; l <= j; l++) {
+            const int n = k + l;
+            if (n & 1) continue;
+            double bk = 1, bl = 1;
+            for (int q = 0; q < k; q++) bk = bk * (i - q) / (q + 1);
+            for (int q = 0; q < l; q++) bl = bl * (j - q) / (q + 1);
+            s += bk * bl * pow(P - A, i - k) * pow(P - B, j - l) * tgamma(0.5 * (n + 1)) / pow(p, 0.5 * (n + 1));
+        }
+    return s;
+}
+
+/* 1-D kinetic element <i| -1/2 d^2/dx^2 |j> with d^2/dx^2 acting on the
+ * right-hand Gaussian of exponent b:
+ *   -1/2 [ j(j-1) s(i,j-2) - 2b(2j+1) s(i,j) + 4b^2 s(i,j+2) ].           */
+static double kin_1d(int i, int j, double A, double B, double P, double a, double b)
+{
+    const double p = a + b;
+    double t = -2.0 * b * (2 * j + 1) * ov_1d(i, j, A, B, P, p) + 4.0 * b * b * ov_1d(i, j + 2, A, B, P, p);
+    if (j >= 2) t += j * (j - 1) * ov_1d(i, j - 2, A, B, P, p);
+    return -0.5 * t;
+}
+
+/* T_mn = sum over the pair list of the local kinetic integrals (component
+ * factors included), T = Tx Sy Sz + Sx Ty Sz + Sx Sy Tz per primitive pair. */
+void orc_kinetic(const orc_basis *bs, double *T)
+{
+    int *off = (int *)malloc(sizeof(int) * bs->nshell);
+    int nbf = ao_offsets(bs, off);
+    memset(T, 0, sizeof(double) * nbf * nbf);
+    lp_list L = build_lps(bs, NULL, 0);
+    for (long q = 0; q < L.n; q++) {
+        const orc_lp *x = &L.v[q];
+        int la = bs->l[x->I], lb = bs->l[x->J];
+        for (int ia = 0; ia < ncart(la); ia++) {
+            int ca[3];
+            cart_comp(la, ia, ca);
+            for (int ib = 0; ib < ncart(lb); ib++) {
+                int cb[3];
+                cart_comp(lb, ib, cb);
+                double s[3], t[3];
+                for (int k = 0; k < 3; k++) {
+                    s[k] = ov_1d(ca[k], cb[k], x->A[k], x->B[k], x->P[k], x->p);
+                    t[k] = kin_1d(ca[k], cb[k], x->A[k], x->B[k], x->P[k], x->a, x->b);
+                }
+                double v = t[0] * s[1] * s[2] + s[0] * t[1] * s[2] + s[0] * s[1] * t[2];
+                T[(long)(off[x->I] + ia) * nbf + off[x->J] + ib] += x->K * comp_factor(la, ia) * comp_factor(lb, ib) * v;
+            }
+        }
+    }
+    free(L.v);
+    free(off);
+}
+
+/* Nuclear attraction of point charges Z_C at C with all their images,
+ *   V_mn = - sum_C Z_C sum_{R_C} < mu | 1/|r - C - R_C| | nu(R) >,
+ * Ewald-split as in Eq. boys_function_split / pbc_v1e_base_case_final:
+ *   real part: (2 pi / p) K sum_t E^{ab}_t R_t(P - C - R_C) with seeds
+ *     s_m = (-2p)^m F_m(p X^2) - c (-2 a_w)^m F_m(a_w X^2),
+ *     a_w = p w^2 / (p + w^2), c = w / sqrt(p + w^2);
+ *   reciprocal part: (4 pi / V) sum_{G != 0} e^{-G^2/4w^2}/G^2
+ *     Re[conj(rho_mn(G)) rho_N(G)],  rho_N(G) = sum_C Z_C e^{-iG.C};
+ *   self term (Eq. v1e_self_term summed over primitives and images):
+ *     -(pi/(V w^2)) S_mn per unit charge.
+ * Every part carries the overall -Z_C of the attraction.  parts: bit0 real,
+ * bit1 reciprocal, bit2 self term, bit3 molecular (bare Coulomb of the
+ * charges at C only, no images; the other bits are then ignored).         */
+typedef struct {
+    double R[RDIM][RDIM][RDIM];
+    int L;
+    double X0[3];
+    double p, omega;
+    int bare;
+} nv_ctx;
+
+static void nuc_seeds(int L, double p, double omega, int bare, double X2, double *s)
+{
+    double F[RDIM + 1];
+    orc_boys(L, p * X2, F);
+    double f = 1.0;
+    for (int m = 0; m <= L; m++) { s[m] = f * F[m]; f *= -2.0 * p; }
+    if (!bare) {
+        const double aw = p * omega * omega / (p + omega * omega), c = omega / sqrt(p + omega * omega);
+        orc_boys(L, aw * X2, F);
+        f = 1.0;
+        for (int m = 0; m <= L; m++) { s[m] -= c * f * F[m]; f *= -2.0 * aw; }
+    }
+}
+
+static void nv_cb(const int *n, const double *RC, void *ud)
+{
+    (void)n;
+    nv_ctx *c = (nv_ctx *)ud;
+    double X[3] = {c->X0[0] - RC[0], c->X0[1] - RC[1], c->X0[2] - RC[2]};
+    double s[RDIM + 1], Rt[RDIM][RDIM][RDIM];
+    nuc_seeds(c->L, c->p, c->omega, c->bare, X[0] * X[0] + X[1] * X[1] + X[2] * X[2], s);
+    md_R(c->L, s, X, Rt);
+    for (int t = 0; t <= c->L; t++)
+        for (int u = 0; u <= c->L - t; u++)
+            for (int v = 0; v <= c->L - t - u; v++) c->R[t][u][v] += Rt[t][u][v];
+}
+
+void orc_nuclear(const orc_basis *bs, int natom, const double *Z, const double *xyz, int parts, double *Vm)
+{
+    int *off = (int *)malloc(sizeof(int) * bs->nshell);
+    int nbf = ao_offsets(bs, off);
+    long n2 = (long)nbf * nbf;
+    memset(Vm, 0, sizeof(double) * n2);
+    lp_list L = build_lps(bs, NULL, 0);
+    const double V = cell_volume(bs->lat), w = bs->omega;
+    const int molecular = (parts & 8) != 0;
+    if (molecular || (parts & 1)) {
+        for (long q = 0; q < L.n; q++) {
+            const orc_lp *x = &L.v[q];
+            int la = bs->l[x->I], lb = bs->l[x->J], Lt = la + lb;
+            double E[3][ORC_MAXL + 1][ORC_MAXL + 1][2 * ORC_MAXL + 2];
+            for (int k = 0; k < 3; k++) md_E(la, lb, x->P[k] - x->A[k], x->P[k] - x->B[k], x->p, E[k]);
+            for (int C = 0; C < natom; C++) {
+                nv_ctx c;
+                memset(&c, 0, sizeof c);
+                c.L = Lt;
+                c.p = x->p;
+                c.omega = w;
+                c.bare = molecular;
+                for (int k = 0; k < 3; k++) c.X0[k] = x->P[k] - xyz[3 * C + k];
+                if (molecular) {
+                    double R0[3] = {0, 0, 0};
+                    int n0[3] = {0, 0, 0};
+                    nv_cb(n0, R0, &c);
+                } else {
+                    const double aw = x->p * w * w / (x->p + w * w), cw = w / sqrt(x->p + w * w);
+                    const double arg = 2.0 * ORC_PI / x->p * fabs(x->K) * (1.0 - cw) * fabs(Z[C]) / bs->delta;
+                    const double r = (arg > 1.0 ? sqrt(log(arg) / aw) : 0.0) + bs->margin;
+                    lattice_sphere(bs->lat, c.X0, r, nv_cb, &c);
+                }
+                const double pref = -Z[C] * 2.0 * ORC_PI / x->p * x->K;
+                for (int ia = 0; ia < ncart(la); ia++) {
+                    int a[3];
+                    cart_comp(la, ia, a);
+                    for (int ib = 0; ib < ncart(lb); ib++) {
+                        int b[3];
+                        cart_comp(lb, ib, b);
+                        double v = 0;
+                        for (int tx = 0; tx <= a[0] + b[0]; tx++)
+                            for (int ty = 0; ty <= a[1] + b[1]; ty++)
+                                for (int tz = 0; tz <= a[2] + b[2]; tz++)
+                                    v += E[0][a[0]][b[0]][tx] * E[1][a[1]][b[1]][ty] * E[2][a[2]][b[2]][tz] * c.R[tx][ty][tz];
+                        Vm[(long)(off[x->I] + ia) * nbf + off[x->J] + ib] += pref * comp_factor(la, ia) * comp_factor(lb, ib) * v;
+                    }
+                }
+            }
+        }
+    }
+    if (!molecular && (parts & 2)) {
+        g_list GL = half_space_G(bs->lat, oracle_gmax(bs));
+        double complex *M = (double complex *)malloc(sizeof(double complex) * n2);
+        for (long g = 0; g < GL.n; g++) {
+            const double *G = GL.g + 3 * g;
+            memset(M, 0, sizeof(double complex) * n2);
+            for (long q = 0; q < L.n; q++) add_pair_ft(bs, &L.v[q], off, G, nbf, M);
+            double complex rn = 0;
+            for (int C = 0; C < natom; C++)
+                rn += Z[C] * cexp(-_Complex_I * (G[0] * xyz[3 * C] + G[1] * xyz[3 * C + 1] + G[2] * xyz[3 * C + 2]));
+            const double wg = 2.0 * 4.0 * ORC_PI / V * recip_weight(bs, G); /* +G and -G */
+            for (long k = 0; k < n2; k++) Vm[k] -= wg * creal(conj(M[k]) * rn);
+        }
+        free(M);
+        free(GL.g);
+    }
+    if (!molecular && (parts & 4) && !isinf(w) && w > 0) {
+        double *S = (double *)malloc(sizeof(double) * n2), Zt = 0;
+        orc_overlap(bs, S);
+        for (int C = 0; C < natom; C++) Zt += Z[C];
+        const double c = ORC_PI / (V * w * w) * Zt; /* -Z times the self term -(pi/(V w^2)) S */
+        for (long k = 0; k < n2; k++) Vm[k] += c * S[k];
+        free(S);
+    }
+    free(L.v);
+    free(off);
+}

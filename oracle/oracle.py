@@ -83,6 +83,8 @@ def lib():
             _lib.orc_ewald_point_charges.restype = ctypes.c_double
             _lib.orc_num_threads.restype = ctypes.c_int
             _lib.orc_jk_sample.argtypes = [B, dp, ctypes.c_int, ctypes.c_int, dp]
+            _lib.orc_kinetic.argtypes = [B, dp]
+            _lib.orc_nuclear.argtypes = [B, ctypes.c_int, dp, dp, ctypes.c_int, dp]
     return _lib
 
 
@@ -191,6 +193,34 @@ def eri_tensor(cell, omega=None, parts=7, delta=ORACLE_DELTA, margin=ORACLE_MARG
     eri = np.zeros((n, n, n, n))
     lib().orc_eri_tensor(b.ref(), int(parts), _dp(eri))
     return eri
+
+
+def kinetic(cell) -> np.ndarray:
+    """Gamma kinetic-energy matrix over the pair list (local integrals of
+    -1/2 nabla^2 from 1-D overlaps; Section 2.1 and its Supporting
+    Information)."""
+    b = Basis(cell)
+    T = np.zeros((b.nbf, b.nbf))
+    lib().orc_kinetic(b.ref(), _dp(T))
+    return T
+
+
+PART_MOLECULAR = 8
+
+
+def nuclear(cell, Z=None, xyz=None, omega=None, parts=7, delta=ORACLE_DELTA, margin=ORACLE_MARGIN) -> np.ndarray:
+    """Nuclear attraction of point charges Z at xyz (default: the cell's
+    atoms) with their images, Ewald-split at omega (Section 2.2, Eq.
+    pbc_v1e_base_case_final): parts bit0 real, bit1 reciprocal, bit2 self
+    term; PART_MOLECULAR alone gives the bare molecular attraction."""
+    import synthcells as sc
+
+    Z = np.ascontiguousarray(sc.nuclear_charges(cell) if Z is None else Z, dtype=np.float64)
+    xyz = np.ascontiguousarray(cell.positions if xyz is None else xyz, dtype=np.float64).reshape(-1)
+    b = Basis(cell, omega=omega, delta=delta, margin=margin)
+    V = np.zeros((b.nbf, b.nbf))
+    lib().orc_nuclear(b.ref(), len(Z), _dp(Z), _dp(xyz), int(parts), _dp(V))
+    return V
 
 
 def jk_from_eri(eri, D):

@@ -4,11 +4,12 @@ Holds no arithmetic of the J/K method: only geometry, basis draws and
 Gaussian matrices.  See ``cells.py``.
 """
 from .cells import (BOHR_PER_ANGSTROM, Cell, Shell, config, density_from_overlap, density_perturbation,
-                    diamond_cell, large_cell, ncart, serving_requests, small_random_cell, tiny_cell, water_cell)
+                    diamond_cell, large_cell, ncart, nuclear_charges, serving_requests, small_random_cell, tiny_cell,
+                    water_cell)
 from .rng import MASTER_SEED, Stream, stream
 
 __all__ = [
     "BOHR_PER_ANGSTROM", "Cell", "Shell", "config", "density_from_overlap", "density_perturbation", "diamond_cell",
-    "large_cell", "ncart", "serving_requests", "small_random_cell", "tiny_cell", "water_cell", "MASTER_SEED",
+    "large_cell", "ncart", "nuclear_charges", "serving_requests", "small_random_cell", "tiny_cell", "water_cell", "MASTER_SEED",
     "Stream", "stream",
 ]

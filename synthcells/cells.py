@@ -263,6 +263,16 @@ def small_random_cell(seed: int, natom: int = 2, lmax: int = 2, skew: bool = Tru
 MASTER_SEED_SMALL = 2410022278 + 100
 
 
+# nuclear charges of the cells' atoms (the synthetic "X" atoms of the tiny
+# and small cells carry 2, so that the tiny cell with 2 occupied orbitals is
+# neutral)
+NUCLEAR_CHARGE = {"H": 1.0, "C": 6.0, "O": 8.0, "X": 2.0}
+
+
+def nuclear_charges(cell: Cell) -> np.ndarray:
+    return np.array([NUCLEAR_CHARGE[s] for s in cell.symbols], dtype=np.float64)
+
+
 def config(index: int, **kw) -> Cell:
     """The synthetic stand-in for workload ``index`` (1 tiny, 2 water,
     3 diamond 3x3x3, 5 diamond 6x6x6)."""
