@@ -62,7 +62,7 @@ typedef struct {
 /* The four lattice-sum thresholds of Section 3.6 (values <= 0 select the
  * paper's default 1e-14) and the mixed-precision switch (Section 3.5):
  * an image quartet whose density-weighted size estimate is at or above
- * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: 1e-4). */
+ * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: 3e-4). */
 typedef struct {
     double pair_R;   /* delta_pair-R, Eq. pbc_eri_pair_cutoff_implementation */
     double pair_cs;  /* delta_pair-Cauchy-Schwarz, Eq. pbc_eri_cauchy_schwarz_cutoff_implementation */
@@ -210,6 +210,23 @@ int jk_build_counts(jk_plan *plan, long long *counts, int n);
 /* Gamma overlap over the plan's pair list (Eq. pbc_overlap_formula),
  * written to the device pointer S (nbf*nbf FP64); stream-ordered. */
 int jk_overlap(const jk_plan *plan, double *S, void *cuda_stream);
+
+/* One-electron operators of the cell on the plan's pair list (paper
+ * Sections 2.1-2.2; the kinetic formula is in its Supporting Information):
+ * T = kinetic energy, sum over images R of <mu| -1/2 nabla^2 |nu(R)>;
+ * V = attraction of point charges Z (host, natom) at xyz (host, natom x 3,
+ * bohr) with all their images, Ewald-split at the plan's omega as in Eq.
+ * pbc_v1e_base_case_final: erfc real-space sum over charge images, the
+ * reciprocal sum against rho_N(G) = sum_C Z_C e^{-iG.C} (G list and
+ * structure factors of the plan), and the self term +(pi/(V w^2)) Z_tot S.
+ * T and V are device pointers (nbf x nbf, row-major, FP64; either may be
+ * NULL); the caller owns them.  Uses the plan's build workspace, so it is
+ * ordered after earlier builds on the plan; synchronises `cuda_stream`
+ * before returning.  With the electron density D, E_kin = sum D o T and
+ * E_ne = sum D o V; the nuclear repulsion is jk_ewald_point_charges.
+ * Errors: JK_ERR_INVALID (NULL plan, natom < 0, charges missing),
+ * JK_ERR_OOM, JK_ERR_CUDA. */
+int jk_one_electron(jk_plan *plan, int natom, const double *Z, const double *xyz, double *T, double *V, void *cuda_stream);
 
 /* Ewald energy of point charges (Eq. nuclear_repulsion_energy, including the
  * removed K = 0 term -(4 pi/V)/(4 w^2) that a non-neutral set needs), on the

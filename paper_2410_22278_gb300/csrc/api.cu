@@ -246,6 +246,22 @@ int jk_overlap(const jk_plan *plan, double *S, void *cuda_stream)
     return JK_OK;
 }
 
+int jk_one_electron(jk_plan *plan, int natom, const double *Z, const double *xyz, double *T, double *V, void *cuda_stream)
+{
+    if (!plan || natom < 0 || (V && natom > 0 && (!Z || !xyz))) return fail(JK_ERR_INVALID, "bad one-electron arguments");
+    try {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        if (cudaSetDevice(plan->p->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+        std::lock_guard<std::mutex> g(plan->p->build_mu);
+        cudaStreamWaitEvent(st, plan->done, 0);
+        int rc = jk::one_electron(plan->p, natom, Z, xyz, T, V, st);
+        cudaEventRecord(plan->done, st);
+        return rc;
+    } catch (...) {
+        return fail(JK_ERR_INVALID, "unexpected host exception");
+    }
+}
+
 int jk_ewald_point_charges(const jk_cell *cell, int n, const double *q, const double *xyz, double omega, double delta, double *energy)
 {
     if (!cell || !q || !xyz || !energy || n <= 0 || !(omega > 0)) return fail(JK_ERR_INVALID, "bad point-charge arguments");

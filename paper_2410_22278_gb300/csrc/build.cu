@@ -135,6 +135,12 @@ __global__ void k_gauss_table(int npv, const double *__restrict__ pv, const doub
     tab[e] = (kPi / p) * sqrt(kPi / p) * exp(-G2 / (4.0 * p));
 }
 
+void launch_gauss_table(const Plan *P, int g0, int gcur, double *tab, cudaStream_t st)
+{
+    const long long ne = (long long)P->pvals.size() * gcur;
+    if (ne > 0) k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, tab);
+}
+
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
 static int cuda_check(const char *what)

@@ -82,6 +82,10 @@ constexpr long long per_prim_quartet(int LA, int LB, int LC, int LD)
     return f;
 }
 
+// screening of one primitive quartet (radius test of Eq. pbc_eri_real_cutoff
+// definition before the images: alpha_w, c_w, prefactor, log)
+constexpr long long per_prim_screen() { return 16; }
+
 // one bra primitive pair per quartet call (bra E coefficients)
 constexpr long long per_bra_prim(int LA, int LB) { return 3 * herm_E(LA, LB) + 1; }
 

@@ -183,6 +183,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             const float awf = 1.0f / (ipf + iqf + iw2);
             const float cwf = sqrtf(awf * (ipf + iqf));
             const float preff = 34.986836655249725f * xf.K * yf.K * ipf * iqf * rsqrtf(xf.p + yf.p);
+            fl += flops::per_prim_screen();
 
             const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
             if (!(lg > 0.0f)) continue;

@@ -220,7 +220,11 @@ __device__ __forceinline__ void boys_attenuated(T Tt, T c, const T *__restrict__
         }
     } else {
         const T s = sqrt(Tt);
-        G[0] = T(0.88622692545275801365) / s * (erfc_(c * s) - erfc_(s));
+        // erfc(s) < 2.2e-17 for s >= 6: below the rounding of erfc(c s) in
+        // every term that passes screening, and an erfc saved
+        T es = T(0);
+        if (s < T(6)) es = erfc_(s);
+        G[0] = T(0.88622692545275801365) / s * (erfc_(c * s) - es);
         T cp = c;
         const T h = T(0.5) / Tt;
 #pragma unroll

@@ -400,10 +400,11 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     if (!(c.pair_cs > 0)) c.pair_cs = 1e-14;
     if (!(c.ewald_R > 0)) c.ewald_R = 1e-14;
     if (!(c.ewald_K > 0)) c.ewald_K = 1e-14;
-    // 1e-4 by default: ten times the paper's switch-over value (Section 3.5);
-    // on the 64-water box it keeps mixed within 3e-10 of FP64 in J, K and E
-    // and sends 0.04% of the image quartets to FP64
-    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 1e-4;
+    // 3e-4 by default, thirty times the paper's switch-over value (Section
+    // 3.5): this GPU's FP64 rate is 1/64 of its FP32 rate (about 1/2 on the
+    // paper's GPU); on the 64-water box mixed stays within 1e-9 of FP64 in
+    // J and K and 3e-10 Ha in E
+    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 3e-4;
     P->cut = c;
 
     // ---- shells, normalised coefficients, component factors
@@ -440,6 +441,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     };
     std::vector<SpiRec> spis;
     std::vector<std::vector<PpiRec>> spi_ppis;
+    std::vector<std::vector<double2>> spi_ab;  // exponents (a, b) of each primitive pair, same order
     const double *L = P->L;
     for (int I = 0; I < nshell; ++I) {
         const ShellRec &sI = P->shells[I];
@@ -492,6 +494,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                 double A[3] = {sF.c[0], sF.c[1], sF.c[2]}, B[3] = {sS.c[0] + R[0], sS.c[1] + R[1], sS.c[2] + R[2]};
                 double AB2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
                 std::vector<PpiRec> pv;
+                std::vector<double2> abv;
                 double Q = 0;
                 for (auto &pr : kv.second) {
                     int pa = swap ? pr.second : pr.first, pb = swap ? pr.first : pr.second;
@@ -506,9 +509,22 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                     x.pad = 1.0 / p;
                     x.K = cn[sF.p0 + pa] * cn[sS.p0 + pb] * std::exp(-a * b / p * AB2);
                     pv.push_back(x);
+                    abv.push_back(make_double2(a, b));
                     Q += std::pow(2.0, 0.25) * std::fabs(x.K) * std::pow(kPi / p, 1.25);  // Eq. 445 per primitive
                 }
-                std::sort(pv.begin(), pv.end(), [](const PpiRec &u, const PpiRec &v) { return std::fabs(u.K) > std::fabs(v.K); });
+                {
+                    std::vector<int> ord(pv.size());
+                    std::iota(ord.begin(), ord.end(), 0);
+                    std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return std::fabs(pv[u].K) > std::fabs(pv[v].K); });
+                    std::vector<PpiRec> pv2;
+                    std::vector<double2> ab2;
+                    for (int o : ord) {
+                        pv2.push_back(pv[o]);
+                        ab2.push_back(abv[o]);
+                    }
+                    pv.swap(pv2);
+                    abv.swap(ab2);
+                }
                 SpiRec sr{};
                 sr.I = F;
                 sr.J = S;
@@ -533,6 +549,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                 sr.pmin = (float)(pmin * (1.0 - 1e-6));
                 spis.push_back(sr);
                 spi_ppis.push_back(std::move(pv));
+                spi_ab.push_back(std::move(abv));
             }
         }
     }
@@ -569,6 +586,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
         SpiRec s = spis[idx];
         s.pp0 = (int)P->ppi.size();
         for (auto &x : spi_ppis[idx]) P->ppi.push_back(x);
+        for (auto &e : spi_ab[idx]) P->ppi_ab.push_back(e);
         P->spi.push_back(s);
     }
     for (int cl = 0; cl < JK_NCLASS_MAX; ++cl) {
@@ -841,6 +859,7 @@ int finish_plan_device(Plan *P)
             const long double t = 2.0L * 3.141592653589793238462643383279502884L * k / 1024.0L;
             ph[k] = make_double2((double)std::cos(t), (double)std::sin(t));
         }
+        if ((rc = upload(P->ppi_ab, &P->d_ppi_ab, b))) return rc;
         if ((rc = upload(P->pvals, &P->d_pvals, b)) || (rc = upload(P->ppi_pidx, &P->d_ppi_pidx, b)) || (rc = upload(gt0, &P->d_gtab0, b)) ||
             (rc = upload(ph, &P->d_phase, b)))
             return rc;
@@ -859,7 +878,7 @@ void destroy_plan(Plan *P)
     if (!P) return;
     cudaSetDevice(P->device);
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
-                    P->d_g0, P->d_compf, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->ws.gtab, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
+                    P->d_g0, P->d_compf, P->d_ppi_ab, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->ws.gtab, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
                     P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
                     P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
                     P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};

@@ -126,6 +126,8 @@ struct Plan {
     // each primitive pair, (cos, sin)(2 pi k / 1024), and (pi/p)^{3/2} (G = 0)
     std::vector<double> pvals;
     std::vector<int> ppi_pidx;
+    std::vector<double2> ppi_ab;  // exponents (a, b) of each primitive pair (one-electron operators)
+    double2 *d_ppi_ab = nullptr;
     double *d_pvals = nullptr, *d_gtab0 = nullptr;
     int *d_ppi_pidx = nullptr;
     double2 *d_phase = nullptr;
@@ -152,6 +154,9 @@ int ozaki_prepare_lowrank(Plan *P, cudaStream_t st);
 int ozaki_exchange_chunk(Plan *P, int m2, int S, cudaStream_t st);
 int ozaki_setup_tc(Plan *P);
 int ozaki_finish(Plan *P, cudaStream_t st);
+struct Plan;
+void launch_gauss_table(const Plan *P, int g0, int gcur, double *tab, cudaStream_t st);
+int one_electron(Plan *P, int natom, const double *Z, const double *xyz, double *T, double *V, cudaStream_t st);
 int energy_noalloc(const Plan *P, const double *D, const double *J, const double *K, double *e_coul, double *e_exch,
                    cudaStream_t st);
 

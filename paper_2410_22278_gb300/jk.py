@@ -33,7 +33,7 @@ JK_MIXED = 1
 # every symbol declared in include/jk.h
 EXPORTS = [
     "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_build_counts", "jk_autotune", "jk_energy",
-    "jk_energy_noalloc",
+    "jk_energy_noalloc", "jk_one_electron",
     "jk_overlap", "jk_ewald_point_charges", "jk_server_create", "jk_submit", "jk_wait", "jk_server_destroy",
     "jk_status_string", "jk_last_error", "jk_microbench_fma",
 ]
@@ -99,6 +99,7 @@ def lib():
         L.jk_autotune.argtypes = [vp, vp, vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
         L.jk_energy.argtypes = [vp, vp, vp, vp, dp, dp, vp]
         L.jk_energy_noalloc.argtypes = [vp, vp, vp, vp, dp, dp, vp]
+        L.jk_one_electron.argtypes = [vp, ctypes.c_int, dp, dp, vp, vp, vp]
         L.jk_overlap.argtypes = [vp, vp, vp]
         L.jk_ewald_point_charges.argtypes = [ctypes.POINTER(jk_cell), ctypes.c_int, dp, dp, ctypes.c_double,
                                              ctypes.c_double, dp]
@@ -255,6 +256,14 @@ class Plan:
         _check(lib().jk_energy_noalloc(self._h, D_ptr, J_ptr or None, K_ptr or None, ctypes.byref(ej), ctypes.byref(ek),
                                        stream or None), "jk_energy_noalloc")
         return ej.value, ek.value
+
+    def one_electron(self, Z, xyz, T_ptr: int, V_ptr: int, stream: int = 0):
+        """Kinetic-energy and nuclear-attraction matrices (jk_one_electron)
+        into device buffers; Z (natom) and xyz (natom x 3, bohr) on the host."""
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+        _check(lib().jk_one_electron(self._h, len(Z), _dp(Z), _dp(xyz), T_ptr or None, V_ptr or None, stream or None),
+               "jk_one_electron")
 
     def overlap(self, S_ptr: int, stream: int = 0):
         _check(lib().jk_overlap(self._h, S_ptr, stream or None), "jk_overlap")
