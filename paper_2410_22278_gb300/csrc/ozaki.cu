@@ -12,9 +12,11 @@
 // product over K <= 1024 terms sums integers of magnitude at most 2^14, so
 // its sum stays within 2^24 and is exact in the FP32 accumulator of the
 // tensor-core MMA; the products with s + t <= S - 1 (0-based) are combined
-// with their power-of-two scales in a compensated single-precision pair.  This is the error-free splitting of Ozaki, Ogita,
-// Oishi and Rump (Numer. Algorithms 59, 2012) with digits sized to the FP32
-// accumulator.
+// with their power-of-two scales in a compensated single-precision pair.
+// This is the error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer.
+// Algorithms 59, 2012) with digits sized to the FP32 accumulator.  The
+// GEMMs run on the tcgen05 tensor cores (TMA operand tiles, accumulators
+// and the compensated pairs in tensor memory; k_ozaki_tc below).
 //
 // Two factorisations of the contraction:
 //   dense:    Zt_b = (D M_b)^T, then K += sum_b M_b Z_b;
@@ -30,7 +32,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -41,25 +42,7 @@ namespace jk {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32, LDS = BK + 8;  // smem row stride in bf16
-constexpr int KFLUSH = 1024;                               // exactness bound of the FP32 accumulator
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint32_t *b)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+constexpr int KFLUSH = 1024;  // exactness bound of the FP32 accumulator
 
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
 {
@@ -119,188 +102,8 @@ __global__ void k_ozaki_slice(const double *__restrict__ X, int rows, int cols, 
     }
 }
 
-struct GemmArgs {
-    const __nv_bfloat16 *A;
-    const int *Aex;
-    long long a_bstride;  // elements between batches (0: shared operand)
-    int a_exb;            // exponents between batches
-    int a_rows_pad;       // rows per slice block
-    const __nv_bfloat16 *B;
-    const int *Bex;
-    long long b_bstride;
-    int b_exb;
-    int b_rows_pad;
-    int kpad;             // row length (K stride) of both operands
-    int koff, klen;       // K range used
-    int S, nb, bsplit, ntm, ntn;
-    double *out;
-    int out_rows, out_cols;
-    long long o_bstride;
-    int ldo, transpose;
-    float sign;
-};
-
-// MODE 0: blockIdx.z = b; out_b = A_b B_b (A may be shared), written as FP64
-// (transposed if requested).  MODE 1: blockIdx.z = split index over b;
-// out += sign sum_b A_b B_b over upper tiles (ntm == ntn), FP64 atomics,
-// mirrored below the diagonal.
-template <int MODE>
-__global__ void __launch_bounds__(256, 1) k_ozaki_gemm(GemmArgs g)
-{
-    __shared__ __align__(16) __nv_bfloat16 sA[2][BM * LDS];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][BN * LDS];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gi = lane >> 2, tig = lane & 3;
-    const int wm = warp >> 2, wn = warp & 3;
-    int mi, nj, b0, b1;
-    if (MODE == 0) {
-        mi = blockIdx.x % g.ntm;
-        nj = blockIdx.x / g.ntm;
-        b0 = blockIdx.z;
-        b1 = b0 + 1;
-    } else {
-        int t = blockIdx.x;
-        mi = 0;
-        while (t >= g.ntm - mi) {
-            t -= g.ntm - mi;
-            ++mi;
-        }
-        nj = mi + t;
-        const int per = (g.nb + g.bsplit - 1) / g.bsplit;
-        b0 = blockIdx.z * per;
-        b1 = min(g.nb, b0 + per);
-    }
-    const int row0 = mi * BM, col0 = nj * BN;
-    float hi[4][4][4], lo[4][4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) hi[a][c][e] = lo[a][c][e] = 0.f;
-
-    for (int b = b0; b < b1; ++b) {
-        const __nv_bfloat16 *Ab = g.A + (size_t)b * g.a_bstride;
-        const int *Aeb = g.Aex + (size_t)(g.a_bstride ? b : 0) * g.a_exb;
-        const __nv_bfloat16 *Bb = g.B + (size_t)b * g.b_bstride;
-        const int *Beb = g.Bex + (size_t)(g.b_bstride ? b : 0) * g.b_exb;
-        int rex[4][2], cex[4][2];
-#pragma unroll
-        for (int mt = 0; mt < 4; ++mt) {
-            rex[mt][0] = Aeb[row0 + wm * 64 + mt * 16 + gi];
-            rex[mt][1] = Aeb[row0 + wm * 64 + mt * 16 + gi + 8];
-        }
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            cex[nt][0] = Beb[col0 + wn * 32 + nt * 8 + 2 * tig];
-            cex[nt][1] = Beb[col0 + wn * 32 + nt * 8 + 2 * tig + 1];
-        }
-        for (int s = 0; s < g.S; ++s)
-            for (int t = 0; s + t < g.S; ++t) {
-                const __nv_bfloat16 *A = Ab + ((size_t)s * g.a_rows_pad + row0) * g.kpad;
-                const __nv_bfloat16 *Bt = Bb + ((size_t)t * g.b_rows_pad + col0) * g.kpad;
-                for (int kc = g.koff; kc < g.koff + g.klen; kc += KFLUSH) {
-                    const int kend = min(g.koff + g.klen, kc + KFLUSH);
-                    float acc[4][4][4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[a][c][e] = 0.f;
-                    auto load_stage = [&](int buf, int k0) {
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const int chunk = tid + q * 256;
-                            const int r = chunk >> 2, c8 = (chunk & 3) * 8;
-                            cp_async16(&sA[buf][r * LDS + c8], A + (size_t)r * g.kpad + k0 + c8);
-                            cp_async16(&sB[buf][r * LDS + c8], Bt + (size_t)r * g.kpad + k0 + c8);
-                        }
-                        cp_async_commit();
-                    };
-                    load_stage(0, kc);
-                    const int nk = (kend - kc) / BK;
-                    for (int kt = 0; kt < nk; ++kt) {
-                        if (kt + 1 < nk) {
-                            load_stage((kt + 1) & 1, kc + (kt + 1) * BK);
-                            cp_async_wait<1>();
-                        } else {
-                            cp_async_wait<0>();
-                        }
-                        __syncthreads();
-                        const __nv_bfloat16 *a_s = sA[kt & 1], *b_s = sB[kt & 1];
-#pragma unroll
-                        for (int kk = 0; kk < BK; kk += 16) {
-                            uint32_t af[4][4], bf[4][2];
-#pragma unroll
-                            for (int mt = 0; mt < 4; ++mt) {
-                                const int r = wm * 64 + mt * 16 + gi;
-                                af[mt][0] = *reinterpret_cast<const uint32_t *>(&a_s[r * LDS + kk + 2 * tig]);
-                                af[mt][1] = *reinterpret_cast<const uint32_t *>(&a_s[(r + 8) * LDS + kk + 2 * tig]);
-                                af[mt][2] = *reinterpret_cast<const uint32_t *>(&a_s[r * LDS + kk + 8 + 2 * tig]);
-                                af[mt][3] = *reinterpret_cast<const uint32_t *>(&a_s[(r + 8) * LDS + kk + 8 + 2 * tig]);
-                            }
-#pragma unroll
-                            for (int nt = 0; nt < 4; ++nt) {
-                                const int c = wn * 32 + nt * 8 + gi;
-                                bf[nt][0] = *reinterpret_cast<const uint32_t *>(&b_s[c * LDS + kk + 2 * tig]);
-                                bf[nt][1] = *reinterpret_cast<const uint32_t *>(&b_s[c * LDS + kk + 8 + 2 * tig]);
-                            }
-#pragma unroll
-                            for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-                                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt]);
-                        }
-                        __syncthreads();
-                    }
-#pragma unroll
-                    for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int sh = rex[mt][e >> 1] + cex[nt][e & 1] - 14 - 8 * (s + t);
-                                two_sum_add(hi[mt][nt][e], lo[mt][nt][e], ldexpf(acc[mt][nt][e], sh));
-                            }
-                }
-            }
-        if (MODE == 0) {
-            double *O = g.out + (size_t)b * g.o_bstride;
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int i = row0 + wm * 64 + mt * 16 + gi + (e >> 1) * 8;
-                        const int j = col0 + wn * 32 + nt * 8 + 2 * tig + (e & 1);
-                        if (i < g.out_rows && j < g.out_cols)
-                            O[g.transpose ? (size_t)j * g.ldo + i : (size_t)i * g.ldo + j] =
-                                (double)hi[mt][nt][e] + (double)lo[mt][nt][e];
-                        hi[mt][nt][e] = lo[mt][nt][e] = 0.f;
-                    }
-        }
-    }
-    if (MODE == 1) {
-#pragma unroll
-        for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int i = row0 + wm * 64 + mt * 16 + gi + (e >> 1) * 8;
-                    const int j = col0 + wn * 32 + nt * 8 + 2 * tig + (e & 1);
-                    const double v = (double)g.sign * ((double)hi[mt][nt][e] + (double)lo[mt][nt][e]);
-                    if (i < g.out_rows && j < g.out_cols && v != 0.0) {
-                        atomicAdd(g.out + (size_t)i * g.ldo + j, v);
-                        if (mi != nj) atomicAdd(g.out + (size_t)j * g.ldo + i, v);
-                    }
-                }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// The same split-precision GEMMs on the tcgen05 tensor cores.  One CTA per
+// The split-precision GEMMs on the tcgen05 tensor cores.  One CTA per
 // 128 x 128 output tile and range of batches: thread 256 (warp 8) issues
 // the TMA loads of the operand slices (4-stage ring of 128 x 64 BF16 tiles
 // per operand, 128-byte swizzle) and the tcgen05.mma instructions (M = N =
@@ -726,8 +529,6 @@ int ozaki_setup_tc(Plan *P)
 {
     Workspace &w = P->ws;
     w.tc = false;
-    const char *legacy = std::getenv("JK_OZAKI_MMA_SYNC");
-    if (legacy && legacy[0] == '1') return JK_OK;
     const int npad = w.npad, n = P->nbf, S = w.oz_slices;
     const long long big_rows = 2LL * w.gc * S * npad;
     if (!slice_map(&w.tm_Ms, w.Ms, big_rows, npad) || !slice_map(&w.tm_Zd, w.Zs, big_rows, npad) ||
@@ -770,7 +571,7 @@ int ozaki_begin(Plan *P, cudaStream_t st)
     Workspace &w = P->ws;
     const int n = P->nbf;
     slice(w.Dp, n, n, n, 0, w.npad, w.npad, w.oz_slices, 1, w.Ds, w.Dex, st);
-    if (w.tc) cudaMemsetAsync(w.Kpart, 0, (size_t)w.kpart_splits * n * n * sizeof(double), st);
+    cudaMemsetAsync(w.Kpart, 0, (size_t)w.kpart_splits * n * n * sizeof(double), st);
     w.lowrank = false;
     if (!w.solver) return check("density slices");
     if (cusolverDnSetStream(w.solver, st) != CUSOLVER_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cusolverDnSetStream failed");
@@ -799,7 +600,7 @@ int ozaki_prepare_lowrank(Plan *P, cudaStream_t st)
         if (w.eigW_host[i] > 1e-10 * wmax) pos.push_back(i);
     for (int i = 0; i < n; ++i)
         if (w.eigW_host[i] < -1e-10 * wmax) neg.push_back(i);
-    const int rp = ((int)pos.size() + BN - 1) / BN * BN, rn = ((int)neg.size() + BN - 1) / BN * BN;
+    const int rp = ((int)pos.size() + 127) / 128 * 128, rn = ((int)neg.size() + 127) / 128 * 128;
     if (wmax == 0 || rp + rn > (6 * w.npad) / 10) return JK_OK;  // not worth it: dense form
     std::vector<int> idx(rp + rn, 0);
     for (size_t k = 0; k < pos.size(); ++k) idx[k] = pos[k];
@@ -812,7 +613,7 @@ int ozaki_prepare_lowrank(Plan *P, cudaStream_t st)
         k_lowrank_factor<<<(unsigned)((e2 + 255) / 256), 256, 0, st>>>(n, w.eigV, w.eigW, w.eigIdx + rp, (int)neg.size(), rn, w.Ct + e1);
     slice(w.Ct, rp + rn, n, n, 0, rp + rn, w.npad, w.oz_slices, 1, w.Cs, w.Cex, st);
     cudaStreamSynchronize(st);  // idx is a host vector that must outlive the copy
-    if (w.tc && !slice_map(&w.tm_Zl, w.Zs, 2LL * w.gc * w.oz_slices * w.npad, rp + rn))
+    if (!slice_map(&w.tm_Zl, w.Zs, 2LL * w.gc * w.oz_slices * w.npad, rp + rn))
         return fail(JK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the low-rank slices");
     w.lowrank = true;
     w.rpos = rp;
@@ -829,114 +630,71 @@ int ozaki_exchange_chunk(Plan *P, int m2, int S, cudaStream_t st)
     Workspace &w = P->ws;
     const int n = P->nbf, npad = w.npad;
     if (S < 1 || S > w.oz_slices) return fail(JK_ERR_INVALID, "slice count outside 1..oz_slices");
-    const int nt = npad / BM;
+    const int nt = npad / TC_BM, ntri = nt * (nt + 1) / 2;
     PhaseTimer &tm = P->timer;
     const double prods = S * (S + 1) / 2.0;
     int ev = tm.start(8);
     slice(w.M, n, n, n, (long long)n * n, npad, npad, S, m2, w.Ms, w.Mex, st);
     tm.stop(8, ev, 1);
-    const long long ms_b = (long long)S * npad * npad;
     if (!w.lowrank) {
-        // Zt_b = (D M_b)^T
-        GemmArgs z{};
-        z.A = w.Ds; z.Aex = w.Dex; z.a_bstride = 0; z.a_exb = 0; z.a_rows_pad = npad;
-        z.B = w.Ms; z.Bex = w.Mex; z.b_bstride = ms_b; z.b_exb = npad; z.b_rows_pad = npad;
-        z.kpad = npad; z.koff = 0; z.klen = npad; z.S = S; z.nb = m2; z.bsplit = 1; z.ntm = nt; z.ntn = nt;
-        z.out = w.Z; z.out_rows = n; z.out_cols = n; z.o_bstride = (long long)n * n; z.ldo = n; z.transpose = 1; z.sign = 1.f;
+        // Zt_b = (D M_b)^T, as (hi, lo) pairs
+        TcArgs t{};
+        t.a_batch_rows = 0; t.a_slice_rows = npad; t.b_batch_rows = S * npad; t.b_slice_rows = npad;
+        t.Aex = w.Dex; t.a_exb = 0; t.Bex = w.Mex; t.b_exb = npad;
+        t.koff = 0; t.klen = npad; t.S = S; t.nb = m2; t.ntm = nt; t.ntn = nt;
+        t.out = reinterpret_cast<float2 *>(w.Z); t.out_rows = n; t.out_cols = n; t.o_bstride = (long long)n * n; t.ldo = n;
+        t.transpose = 1; t.err = w.err; t.bsplit = tc_splits(nt * nt, m2);
         ev = tm.start(7);
-        if (w.tc) {
-            TcArgs t{};
-            t.a_batch_rows = 0; t.a_slice_rows = npad; t.b_batch_rows = S * npad; t.b_slice_rows = npad;
-            t.Aex = w.Dex; t.a_exb = 0; t.Bex = w.Mex; t.b_exb = npad;
-            t.koff = 0; t.klen = npad; t.S = S; t.nb = m2; t.bsplit = 1; t.ntm = nt; t.ntn = nt;
-            t.out = reinterpret_cast<float2 *>(w.Z); t.out_rows = n; t.out_cols = n; t.o_bstride = (long long)n * n; t.ldo = n;
-            t.transpose = 1; t.err = w.err; t.bsplit = tc_splits(nt * nt, m2);
-            launch_tc(0, w.tm_Ds, w.tm_Ms, t, dim3(nt * nt, 1, t.bsplit), st);
-        } else {
-            k_ozaki_gemm<0><<<dim3(nt * nt, 1, m2), 256, 0, st>>>(z);
-        }
+        launch_tc(0, w.tm_Ds, w.tm_Ms, t, dim3(nt * nt, 1, t.bsplit), st);
         tm.stop(7, ev, 1);
         w.mma_flops += prods * 2.0 * npad * (double)npad * npad * m2;
         ev = tm.start(8);
-        if (w.tc) slice_pair(reinterpret_cast<const float2 *>(w.Z), n, n, n, (long long)n * n, npad, npad, S, m2, w.Zs, w.Zex, st);
-        else slice(w.Z, n, n, n, (long long)n * n, npad, npad, S, m2, w.Zs, w.Zex, st);
+        slice_pair(reinterpret_cast<const float2 *>(w.Z), n, n, n, (long long)n * n, npad, npad, S, m2, w.Zs, w.Zex, st);
         tm.stop(8, ev, 1);
-        // K += sum_b M_b Z_b
-        GemmArgs k{};
-        k.A = w.Ms; k.Aex = w.Mex; k.a_bstride = ms_b; k.a_exb = npad; k.a_rows_pad = npad;
-        k.B = w.Zs; k.Bex = w.Zex; k.b_bstride = ms_b; k.b_exb = npad; k.b_rows_pad = npad;
-        k.kpad = npad; k.koff = 0; k.klen = npad; k.S = S; k.nb = m2; k.ntm = nt; k.ntn = nt;
-        const int ntri = nt * (nt + 1) / 2;
-        k.bsplit = std::max(1, std::min((152 * 2 + ntri - 1) / ntri, m2));
-        k.out = w.KLR; k.out_rows = n; k.out_cols = n; k.ldo = n; k.sign = 1.f;
+        // K += sum_b M_b Z_b, upper tiles into the float-pair partials
+        TcArgs k{};
+        k.a_batch_rows = S * npad; k.a_slice_rows = npad; k.b_batch_rows = S * npad; k.b_slice_rows = npad;
+        k.Aex = w.Mex; k.a_exb = npad; k.Bex = w.Zex; k.b_exb = npad;
+        k.koff = 0; k.klen = npad; k.S = S; k.nb = m2; k.bsplit = std::min(w.kpart_splits, m2); k.ntm = nt; k.ntn = nt;
+        k.part = w.Kpart; k.part_stride = (long long)n * n; k.ldp = n; k.out_rows = n; k.out_cols = n; k.sign = 1.f;
+        k.err = w.err;
         ev = tm.start(7);
-        if (w.tc) {
-            TcArgs t{};
-            t.a_batch_rows = S * npad; t.a_slice_rows = npad; t.b_batch_rows = S * npad; t.b_slice_rows = npad;
-            t.Aex = w.Mex; t.a_exb = npad; t.Bex = w.Zex; t.b_exb = npad;
-            t.koff = 0; t.klen = npad; t.S = S; t.nb = m2; t.bsplit = std::min(w.kpart_splits, m2); t.ntm = nt; t.ntn = nt;
-            t.part = w.Kpart; t.part_stride = (long long)n * n; t.ldp = n; t.out_rows = n; t.out_cols = n; t.sign = 1.f;
-            t.err = w.err;
-            launch_tc(1, w.tm_Ms, w.tm_Zd, t, dim3(ntri, 1, t.bsplit), st);
-        } else {
-            k_ozaki_gemm<1><<<dim3(ntri, 1, k.bsplit), 256, 0, st>>>(k);
-        }
+        launch_tc(1, w.tm_Ms, w.tm_Zd, k, dim3(ntri, 1, k.bsplit), st);
         tm.stop(7, ev, 1);
-        w.mma_flops += prods * 2.0 * BM * (double)BN * npad * ntri * m2;
+        w.mma_flops += prods * 2.0 * TC_BM * (double)TC_BN * npad * ntri * m2;
         return check("split-precision exchange GEMM (dense)");
     }
     const int rt = w.rpos + w.rneg;
-    // Y_b = M_b [C+ C-]  (n x rt, row-major)
-    GemmArgs y{};
-    y.A = w.Ms; y.Aex = w.Mex; y.a_bstride = ms_b; y.a_exb = npad; y.a_rows_pad = npad;
-    y.B = w.Cs; y.Bex = w.Cex; y.b_bstride = 0; y.b_exb = 0; y.b_rows_pad = rt;
-    y.kpad = npad; y.koff = 0; y.klen = npad; y.S = S; y.nb = m2; y.bsplit = 1; y.ntm = nt; y.ntn = rt / BN;
-    y.out = w.Z; y.out_rows = n; y.out_cols = rt; y.o_bstride = (long long)n * rt; y.ldo = rt; y.transpose = 0; y.sign = 1.f;
+    // Y_b = M_b [C+ C-]  (n x rt, row-major, (hi, lo) pairs)
+    TcArgs y{};
+    y.a_batch_rows = S * npad; y.a_slice_rows = npad; y.b_batch_rows = 0; y.b_slice_rows = rt;
+    y.Aex = w.Mex; y.a_exb = npad; y.Bex = w.Cex; y.b_exb = 0;
+    y.koff = 0; y.klen = npad; y.S = S; y.nb = m2; y.ntm = nt; y.ntn = rt / TC_BN;
+    y.out = reinterpret_cast<float2 *>(w.Z); y.out_rows = n; y.out_cols = rt; y.o_bstride = (long long)n * rt; y.ldo = rt;
+    y.transpose = 0; y.err = w.err; y.bsplit = tc_splits(nt * (rt / TC_BN), m2);
     ev = tm.start(7);
-    if (w.tc) {
-        TcArgs t{};
-        t.a_batch_rows = S * npad; t.a_slice_rows = npad; t.b_batch_rows = 0; t.b_slice_rows = rt;
-        t.Aex = w.Mex; t.a_exb = npad; t.Bex = w.Cex; t.b_exb = 0;
-        t.koff = 0; t.klen = npad; t.S = S; t.nb = m2; t.bsplit = 1; t.ntm = nt; t.ntn = rt / BN;
-        t.out = reinterpret_cast<float2 *>(w.Z); t.out_rows = n; t.out_cols = rt; t.o_bstride = (long long)n * rt; t.ldo = rt;
-        t.transpose = 0; t.err = w.err; t.bsplit = tc_splits(nt * (rt / BN), m2);
-        launch_tc(0, w.tm_Ms, w.tm_Cs, t, dim3(nt * (rt / BN), 1, t.bsplit), st);
-    } else {
-        k_ozaki_gemm<0><<<dim3(nt * (rt / BN), 1, m2), 256, 0, st>>>(y);
-    }
+    launch_tc(0, w.tm_Ms, w.tm_Cs, y, dim3(nt * (rt / TC_BN), 1, y.bsplit), st);
     tm.stop(7, ev, 1);
     w.mma_flops += prods * 2.0 * npad * (double)rt * npad * m2;
     ev = tm.start(8);
-    if (w.tc) slice_pair(reinterpret_cast<const float2 *>(w.Z), n, rt, rt, (long long)n * rt, npad, rt, S, m2, w.Zs, w.Zex, st);
-    else slice(w.Z, n, rt, rt, (long long)n * rt, npad, rt, S, m2, w.Zs, w.Zex, st);
+    slice_pair(reinterpret_cast<const float2 *>(w.Z), n, rt, rt, (long long)n * rt, npad, rt, S, m2, w.Zs, w.Zex, st);
     tm.stop(8, ev, 1);
     // K += sum_b Y+_b Y+_b^T - Y-_b Y-_b^T  (symmetric, K range per group)
-    const long long ys_b = (long long)S * npad * rt;
-    const int ntri = nt * (nt + 1) / 2;
     for (int grp = 0; grp < 2; ++grp) {
         const int klen = grp == 0 ? w.rpos : w.rneg;
         if (!klen) continue;
-        GemmArgs k{};
-        k.A = w.Zs; k.Aex = w.Zex; k.a_bstride = ys_b; k.a_exb = npad; k.a_rows_pad = npad;
-        k.B = w.Zs; k.Bex = w.Zex; k.b_bstride = ys_b; k.b_exb = npad; k.b_rows_pad = npad;
-        k.kpad = rt; k.koff = grp == 0 ? 0 : w.rpos; k.klen = klen; k.S = S; k.nb = m2; k.ntm = nt; k.ntn = nt;
-        k.bsplit = std::max(1, std::min((152 * 2 + ntri - 1) / ntri, m2));
-        k.out = w.KLR; k.out_rows = n; k.out_cols = n; k.ldo = n; k.sign = grp == 0 ? 1.f : -1.f;
+        TcArgs k{};
+        k.a_batch_rows = S * npad; k.a_slice_rows = npad; k.b_batch_rows = S * npad; k.b_slice_rows = npad;
+        k.Aex = w.Zex; k.a_exb = npad; k.Bex = w.Zex; k.b_exb = npad;
+        k.koff = grp == 0 ? 0 : w.rpos; k.klen = klen; k.S = S; k.nb = m2; k.bsplit = std::min(w.kpart_splits, m2); k.ntm = nt;
+        k.ntn = nt;
+        k.part = w.Kpart; k.part_stride = (long long)n * n; k.ldp = n; k.out_rows = n; k.out_cols = n;
+        k.sign = grp == 0 ? 1.f : -1.f;
+        k.err = w.err;
         ev = tm.start(7);
-        if (w.tc) {
-            TcArgs t{};
-            t.a_batch_rows = S * npad; t.a_slice_rows = npad; t.b_batch_rows = S * npad; t.b_slice_rows = npad;
-            t.Aex = w.Zex; t.a_exb = npad; t.Bex = w.Zex; t.b_exb = npad;
-            t.koff = k.koff; t.klen = klen; t.S = S; t.nb = m2; t.bsplit = std::min(w.kpart_splits, m2); t.ntm = nt; t.ntn = nt;
-            t.part = w.Kpart; t.part_stride = (long long)n * n; t.ldp = n; t.out_rows = n; t.out_cols = n;
-            t.sign = grp == 0 ? 1.f : -1.f;
-            t.err = w.err;
-            launch_tc(1, w.tm_Zl, w.tm_Zl, t, dim3(ntri, 1, t.bsplit), st);
-        } else {
-            k_ozaki_gemm<1><<<dim3(ntri, 1, k.bsplit), 256, 0, st>>>(k);
-        }
+        launch_tc(1, w.tm_Zl, w.tm_Zl, k, dim3(ntri, 1, k.bsplit), st);
         tm.stop(7, ev, 1);
-        w.mma_flops += prods * 2.0 * BM * (double)BN * klen * ntri * m2;
+        w.mma_flops += prods * 2.0 * TC_BM * (double)TC_BN * klen * ntri * m2;
     }
     return check("split-precision exchange GEMM (low rank)");
 }
