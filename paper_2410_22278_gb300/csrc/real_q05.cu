@@ -9,7 +9,7 @@ void launch_real_q05(const RealLaunch &a)
     const int nb = a.b1 - a.b0, nk = a.k1 - a.k0;
     if (nb <= 0 || nk <= 0) return;
     if (a.list_pass) {
-        k_real_list<0, 0, 2, 2><<<152 * 4, kRealThreads, 0, a.st>>>(a.pl, a.big, a.nbig, a.cap, a.same, a.Dp, a.X, a.Y, a.cnt64);
+        k_real_list<0, 0, 2, 2><<<152 * 8, kRealThreads, 0, a.st>>>(a.pl, a.big, a.nbig, a.cap, a.same, a.Dp, a.X, a.Y, a.cnt64);
         return;
     }
     dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
