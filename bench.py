@@ -145,7 +145,7 @@ def cpu_baseline_sample(cell, D):
     from oracle import oracle as O
 
     t = time.perf_counter()
-    full_s, det = oracle_sample(cell, D)
+    full_s, det = oracle_sample(cell, D, n_bra=160)
     took = time.perf_counter() - t
     return {"value": 1.0 / full_s, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": "%d strided bra local pairs of %d against all kets and 2 of %d G vectors (%.1f s), extrapolated to a "
