@@ -119,7 +119,7 @@ def run_reference(args):
     fulls, samples = [], []
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
-        full_s, det = oracle_sample(cell, D, n_bra=8)
+        full_s, det = oracle_sample(cell, D, n_bra=32)
         if i >= args.warmup:
             fulls.append(full_s)
             samples.append(time.perf_counter() - t)
@@ -131,7 +131,7 @@ def run_reference(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "parallelism": "host cores (OpenMP)", "l2": "n/a"},
         "cpu_baseline": {"value": value, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": "per step: 8 strided bra local pairs of %d against all kets plus 2 of %d G vectors, "
+                         "sample": "per step: 32 strided bra local pairs of %d against all kets plus 2 of %d G vectors, "
                                    "extrapolated to a full build (%.1f s of CPU work per step)"
                                    % (det["local_pairs"], det["n_g"], statistics.mean(samples))},
         "e2e": {"value": value, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -145,7 +145,7 @@ def cpu_baseline_sample(cell, D):
     from oracle import oracle as O
 
     t = time.perf_counter()
-    full_s, det = oracle_sample(cell, D, n_bra=160)
+    full_s, det = oracle_sample(cell, D, n_bra=320)
     took = time.perf_counter() - t
     return {"value": 1.0 / full_s, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": "%d strided bra local pairs of %d against all kets and 2 of %d G vectors (%.1f s), extrapolated to a "

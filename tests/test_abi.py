@@ -101,3 +101,38 @@ def test_plan_create_without_device_fails_cleanly(jk):
     with pytest.raises(jk.JkError) as e:
         jk.plan_from_cell(cell)
     assert e.value.status == jk.JK_ERR_CUDA
+
+
+def test_null_plan_is_rejected_before_any_device_call(jk):
+    """Every entry point that takes a plan answers a NULL plan (or NULL
+    outputs) with JK_ERR_INVALID and touches no device."""
+    import ctypes
+
+    L = jk.lib()
+    e1, e2 = ctypes.c_double(), ctypes.c_double()
+    cnt = (ctypes.c_longlong * 6)()
+    ms = (ctypes.c_double * 11)()
+    nl = ctypes.c_int()
+    tk = ctypes.c_longlong()
+    calls = {
+        "jk_build": lambda: L.jk_build(None, None, None, None, None),
+        "jk_build_host": lambda: L.jk_build_host(None, None, None, None, None),
+        "jk_build_times": lambda: L.jk_build_times(None, ms, ctypes.byref(nl), 11),
+        "jk_build_counts": lambda: L.jk_build_counts(None, cnt, 6),
+        "jk_autotune": lambda: L.jk_autotune(None, None, None, None, None),
+        "jk_energy": lambda: L.jk_energy(None, None, None, None, ctypes.byref(e1), ctypes.byref(e2), None),
+        "jk_energy_noalloc": lambda: L.jk_energy_noalloc(None, None, None, None, ctypes.byref(e1), ctypes.byref(e2), None),
+        "jk_overlap": lambda: L.jk_overlap(None, None, None),
+        "jk_one_electron": lambda: L.jk_one_electron(None, 0, None, None, None, None, None),
+        "jk_plan_info": lambda: L.jk_plan_info(None, None),
+        "jk_submit": lambda: L.jk_submit(None, None, None, None, None, ctypes.byref(tk)),
+        "jk_wait": lambda: L.jk_wait(None, 0, 0, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == jk.JK_ERR_INVALID, name
+    assert L.jk_plan_nbf(None) == -1
+    srv = ctypes.c_void_p()
+    assert L.jk_server_create(0, 1 << 30, 0, ctypes.byref(srv)) == jk.JK_ERR_INVALID
+    assert L.jk_server_create(0, 0, 4, ctypes.byref(srv)) == jk.JK_ERR_INVALID
+    L.jk_plan_destroy(None)
+    L.jk_server_destroy(None)
