@@ -121,24 +121,52 @@ void launch_sfac(int cls, const PlanDev &pl, int sp0, int sp1, const double *gv,
     }
 }
 
+template <int LA, int LB>
+static void sfac_df_go(const PlanDev &pl, int sp0, int sp1, int g0, int gcur, const float2 *gtab, double *M, cudaStream_t st)
+{
+    const long long nt = (long long)(sp1 - sp0) * gcur;
+    if (nt <= 0) return;
+    k_sfac_df<LA, LB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(pl, sp0, sp1, g0, gcur, gtab, M);
+}
+
+static void launch_sfac_df(int cls, const PlanDev &pl, int sp0, int sp1, int g0, int gcur, const float2 *gtab, double *M, cudaStream_t st)
+{
+    switch (cls) {
+    case 0: sfac_df_go<0, 0>(pl, sp0, sp1, g0, gcur, gtab, M, st); break;
+    case 1: sfac_df_go<1, 0>(pl, sp0, sp1, g0, gcur, gtab, M, st); break;
+    case 2: sfac_df_go<1, 1>(pl, sp0, sp1, g0, gcur, gtab, M, st); break;
+    case 3: sfac_df_go<2, 0>(pl, sp0, sp1, g0, gcur, gtab, M, st); break;
+    case 4: sfac_df_go<2, 1>(pl, sp0, sp1, g0, gcur, gtab, M, st); break;
+    case 5: sfac_df_go<2, 2>(pl, sp0, sp1, g0, gcur, gtab, M, st); break;
+    default: break;
+    }
+}
+
 // (pi/p)^{3/2} e^{-G^2/4p} for every distinct pair exponent p and every G of
 // a chunk, laid out [p][g] (consecutive threads of the structure-factor
-// kernel read consecutive g)
+// kernel read consecutive g); into tab (FP64) or, when tab2 is given, into
+// tab2 as double-floats
 __global__ void k_gauss_table(int npv, const double *__restrict__ pv, const double *__restrict__ gv, int g0, int gcur,
-                              double *__restrict__ tab)
+                              double *__restrict__ tab, float2 *__restrict__ tab2)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)npv * gcur) return;
     const int ip = (int)(e / gcur), gi = (int)(e % gcur);
     const double *g = gv + 4 * (size_t)(g0 + gi);
     const double G2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2], p = pv[ip];
-    tab[e] = (kPi / p) * sqrt(kPi / p) * exp(-G2 / (4.0 * p));
+    const double v = (kPi / p) * sqrt(kPi / p) * exp(-G2 / (4.0 * p));
+    if (tab2) {
+        const dfl d = dfl_split(v);
+        tab2[e] = make_float2(d.hi, d.lo);
+    } else {
+        tab[e] = v;
+    }
 }
 
 void launch_gauss_table(const Plan *P, int g0, int gcur, double *tab, cudaStream_t st)
 {
     const long long ne = (long long)P->pvals.size() * gcur;
-    if (ne > 0) k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, tab);
+    if (ne > 0) k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, tab, nullptr);
 }
 
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
@@ -288,6 +316,8 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
 
     // ---- reciprocal space
     const int ng = (int)(P->gvec.size() / 4);
+    // mixed precision: structure factors in double-float on the FP32 pipe
+    const bool sfac_df = mixed && P->sfac_df && w.gtab2;
     if (mixed && K && (rc = ozaki_prepare_lowrank(P, st))) return rc;
     for (int g0 = 0; g0 < ng; g0 += w.gc) {
         const int gcur = std::min(w.gc, ng - g0);
@@ -295,10 +325,14 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
         int nsf = 0;
         {
             const long long ne = (long long)P->pvals.size() * gcur;
-            k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, w.gtab);
+            k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, w.gtab,
+                                                                         sfac_df ? w.gtab2 : nullptr);
         }
         for (int c = 0; c < JK_NCLASS_MAX; ++c) {
-            launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, w.M, st);
+            if (sfac_df)
+                launch_sfac_df(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], g0, gcur, w.gtab2, w.M, st);
+            else
+                launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, w.M, st);
             nsf += P->spair_class_off[c + 1] > P->spair_class_off[c];
         }
         if ((rc = cuda_check("structure factors"))) return rc;

@@ -61,6 +61,21 @@ struct PpiF {        // single-precision copy of a local primitive pair (FP32 ke
     float pad;       // 1/p
 };
 
+// One local primitive pair for the double-float structure factors: the
+// fractional coordinates of P reduced mod 1 and split in three (f1 on the
+// grid 2^-16, f2 on the grid 2^-33, f3 the rest), K, the index of its
+// exponent among the distinct ones, and P - A, P - B and 1/2p as
+// double-floats (hi, lo).
+struct PpiDF {
+    float4 a;  // f1x, f1y, f1z, K hi
+    float4 b;  // f2x, f2y, f2z, K lo
+    float4 c;  // f3x, f3y, f3z, exponent index (int bits)
+    float4 d;  // (P-A)x hi, lo, (P-A)y hi, lo
+    float4 e;  // (P-A)z hi, lo, (P-B)x hi, lo
+    float4 f;  // (P-B)y hi, lo, (P-B)z hi, lo
+    float4 g;  // 1/2p hi, lo, 0, 0
+};
+
 struct SpairRec {    // unique shell pair (I, J) with its images [spi0, spi0 + nspi)
     int I, J, spi0, nspi;
 };
@@ -86,6 +101,9 @@ struct PlanDev {
     const double *compf;         // Cartesian component factor of each AO
     const int *ppi_pidx;         // index of each primitive pair's exponent p among the distinct ones
     const double2 *phase;        // (cos, sin)(2 pi k / 1024), k = 0..1023
+    const PpiDF *ppdf;           // double-float copy of the primitive pairs (mixed-precision structure factors)
+    const float4 *gdf;           // [ng][3]: (n1, n2, n3, 0) with G = sum n_k b_k; (Gx, Gy) and (Gz, 0) as double-floats
+    const float4 *phasef;        // (cos, sin)(2 pi k / 1024) as double-floats (cos hi, cos lo, sin hi, sin lo)
     double L[9];                 // lattice rows a, b, c
     double Finv[9];              // fractional coordinates f = Finv * r
     float Lf[9], Finvf[9];       // the same in single precision (no conversions in FP32 kernels)

@@ -17,6 +17,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
 #include "jk_internal.h"
 #include "flops.h"
 #include "md.cuh"
@@ -788,6 +789,186 @@ __global__ void __launch_bounds__(128) k_sfac(PlanDev pl, int sp0, int sp1, cons
                 const size_t ot = (size_t)(aoJ + b) * n + aoI + a;
                 Mr[ot] = sw * re[a * NB + b];
                 Mi[ot] = sw * im[a * NB + b];
+            }
+        }
+}
+
+
+// E^{ij}_t for one axis in double-float (the recursion of herm_E with
+// E^{00}_0 = 1 folded in at compile time); entries with t > i + j are never
+// read.
+template <int LA, int LB>
+__host__ __device__ __forceinline__ void herm_E_df(dfl PA, dfl PB, dfl oo2p, dfl *E)
+{
+    constexpr int NT = LA + LB + 1;
+#pragma unroll
+    for (int i = 0; i <= LA; ++i)
+#pragma unroll
+        for (int j = 0; j <= LB; ++j) {
+            if (i == 0 && j == 0) continue;
+            const int b = i > 0 ? ((i - 1) * (LB + 1) + j) * NT : (i * (LB + 1) + j - 1) * NT;
+            const int top = i + j - 1;  // highest t of the level below
+            const dfl X = i > 0 ? PA : PB;
+#pragma unroll
+            for (int t = 0; t <= i + j; ++t) {
+                dfl v{0.0f, 0.0f};
+                bool any = false;
+                if (t <= top) {
+                    v = (b + t == 0) ? X : df_mul(X, E[b + t]);
+                    any = true;
+                }
+                if (t > 0) {
+                    const dfl u = (b + t - 1 == 0) ? oo2p : df_mul(oo2p, E[b + t - 1]);
+                    v = any ? df_add(v, u) : u;
+                    any = true;
+                }
+                if (t + 1 <= top) v = df_add(v, df_mulf(E[b + t + 1], (float)(t + 1)));
+                E[(i * (LB + 1) + j) * NT + t] = v;
+            }
+        }
+}
+
+__host__ __device__ __forceinline__ void df_cmul(dfl &xr, dfl &xi, dfl yr, dfl yi)
+{
+    const dfl r = df_sub(df_mul(xr, yr), df_mul(xi, yi));
+    const dfl i = df_add(df_mul(xr, yi), df_mul(xi, yr));
+    xr = r;
+    xi = i;
+}
+
+// One primitive pair's contribution to the Cartesian block of a structure
+// factor, in double-float: with the phase and Gaussian factor (pr, pim)
+// already formed, multiply by the per-axis Hermite polynomials
+// h_k = sum_t E^{ij}_t (-iG_k)^t (Gp[k][t] = G_k^t) and accumulate into
+// re/im; twice adds the transposed block as well (the image (I, I, -R)).
+template <int LA, int LB>
+__host__ __device__ __forceinline__ void sfac_df_poly(const dfl PA[3], const dfl PB[3], dfl oo2p, const dfl (*Gp)[LA + LB + 1], dfl pr,
+                                                      dfl pim, bool twice, dfl *re, dfl *im)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NT = LA + LB + 1;
+    dfl hr[3][(LA + 1) * (LB + 1)], hi[3][(LA + 1) * (LB + 1)];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dfl E[(LA + 1) * (LB + 1) * NT];
+        herm_E_df<LA, LB>(PA[k], PB[k], oo2p, E);
+#pragma unroll
+        for (int i = 0; i <= LA; ++i)
+#pragma unroll
+            for (int j = 0; j <= LB; ++j) {
+                if (i == 0 && j == 0) continue;
+                const int e0 = (i * (LB + 1) + j) * NT;
+                // (-iG)^t: 1, -iG, -G^2, iG^3, G^4
+                dfl ar = E[e0], ai{0.0f, 0.0f};
+#pragma unroll
+                for (int t = 1; t <= i + j; ++t) {
+                    const dfl term = df_mul(E[e0 + t], Gp[k][t]);
+                    if (t == 1) ai = df_neg(term);
+                    else if (t == 2) ar = df_sub(ar, term);
+                    else if (t == 3) ai = df_add(ai, term);
+                    else ar = df_add(ar, term);
+                }
+                hr[k][i * (LB + 1) + j] = ar;
+                hi[k][i * (LB + 1) + j] = ai;
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            dfl vr = pr, vi = pim;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int ia = cexp(LA, a, k), jb = cexp(LB, b, k);
+                if (ia == 0 && jb == 0) continue;
+                df_cmul(vr, vi, hr[k][ia * (LB + 1) + jb], hi[k][ia * (LB + 1) + jb]);
+            }
+            re[a * NB + b] = df_add(re[a * NB + b], vr);
+            im[a * NB + b] = df_add(im[a * NB + b], vi);
+            if (twice) {
+                re[b * NB + a] = df_add(re[b * NB + a], vr);
+                im[b * NB + a] = df_add(im[b * NB + a], vi);
+            }
+        }
+}
+
+// Structure factors of one class of unique shell pairs for a chunk of G, as
+// k_sfac, in double-float arithmetic on the FP32 pipe (mixed precision): the
+// phase from the integer coordinates of G and the split fractional
+// coordinates of P (df_turns, exact reduction mod 2 pi), sin and cos by table
+// and Taylor series, the Gaussian factor from the chunk's double-float table,
+// the Hermite polynomials and the Cartesian products in double-float.
+// Relative accuracy about 1e-14 per term; the result is rounded to FP64.
+template <int LA, int LB>
+__global__ void __launch_bounds__(128) k_sfac_df(PlanDev pl, int sp0, int sp1, int g0, int gcur, const float2 *__restrict__ gtab,
+                                                 double *__restrict__ M)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), L = LA + LB;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int gi = (int)(idx % gcur);
+    const int sp = sp0 + (int)(idx / gcur);
+    if (sp >= sp1) return;
+    const SpairRec rec = pl.spair[sp];
+    const float4 gn = __ldg(pl.gdf + 3 * (size_t)(g0 + gi));
+    dfl Gp[3][L + 1];  // powers of G_k, [k][t] = G_k^t, t >= 1
+    if constexpr (L > 0) {
+        const float4 g1 = __ldg(pl.gdf + 3 * (size_t)(g0 + gi) + 1), g2 = __ldg(pl.gdf + 3 * (size_t)(g0 + gi) + 2);
+        const dfl Gk[3] = {{g1.x, g1.y}, {g1.z, g1.w}, {g2.x, g2.y}};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Gp[k][0] = dfl{1.0f, 0.0f};
+            Gp[k][1] = Gk[k];
+#pragma unroll
+            for (int t = 2; t <= L; ++t) Gp[k][t] = df_mul(Gp[k][t - 1], Gk[k]);
+        }
+    }
+    dfl re[NA * NB], im[NA * NB];
+#pragma unroll
+    for (int k = 0; k < NA * NB; ++k) re[k] = im[k] = dfl{0.0f, 0.0f};
+    const bool diag = rec.I == rec.J;
+    for (int s = 0; s < rec.nspi; ++s) {
+        const SpiRec si = pl.spi[pl.spi_order[rec.spi0 + s]];
+        const bool rzero = si.n[0] == 0 && si.n[1] == 0 && si.n[2] == 0;
+        const bool twice = diag && !rzero;  // the image (I, I, -R) is the transposed block
+        for (int pp = 0; pp < si.npp; ++pp) {
+            const PpiDF *q = pl.ppdf + si.pp0 + pp;
+            const float4 qa = __ldg(&q->a), qb = __ldg(&q->b), qc = __ldg(&q->c);
+            const float f1[3] = {qa.x, qa.y, qa.z}, f2[3] = {qb.x, qb.y, qb.z}, f3[3] = {qc.x, qc.y, qc.z};
+            dfl w, cs, sn;
+            const int j = df_turns(gn.x, gn.y, gn.z, f1, f2, f3, w);
+            df_sincos_turns(w, __ldg(pl.phasef + (j & 1023)), cs, sn);
+            // K (pi/p)^{3/2} e^{-G^2/4p} e^{-iG.P}
+            const float2 gt = __ldg(gtab + (size_t)__float_as_int(qc.w) * gcur + gi);
+            const dfl amp = df_mul(dfl{qa.w, qb.w}, dfl{gt.x, gt.y});
+            const dfl pr = df_mul(amp, cs), pim = df_neg(df_mul(amp, sn));
+            if constexpr (L == 0) {
+                const float f = twice ? 2.0f : 1.0f;  // s-s: the transposed block is the same element
+                re[0] = df_add(re[0], dfl{f * pr.hi, f * pr.lo});
+                im[0] = df_add(im[0], dfl{f * pim.hi, f * pim.lo});
+            } else {
+                const float4 qd = __ldg(&q->d), qe = __ldg(&q->e), qf = __ldg(&q->f), qg = __ldg(&q->g);
+                const dfl PA[3] = {{qd.x, qd.y}, {qd.z, qd.w}, {qe.x, qe.y}};
+                const dfl PB[3] = {{qe.z, qe.w}, {qf.x, qf.y}, {qf.z, qf.w}};
+                sfac_df_poly<LA, LB>(PA, PB, dfl{qg.x, qg.y}, Gp, pr, pim, twice, re, im);
+            }
+        }
+    }
+    const int n = pl.nbf;
+    const double sw = pl.gvec[4 * (g0 + gi) + 3];
+    const int aoI = pl.shells[rec.I].ao, aoJ = pl.shells[rec.J].ao;
+    double *Mr = M + (size_t)(2 * gi) * n * n;
+    double *Mi = Mr + (size_t)n * n;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const double vr = sw * dfl_value(re[a * NB + b]), vi = sw * dfl_value(im[a * NB + b]);
+            const size_t o = (size_t)(aoI + a) * n + aoJ + b;
+            Mr[o] = vr;
+            Mi[o] = vi;
+            if (!diag) {
+                const size_t ot = (size_t)(aoJ + b) * n + aoI + a;
+                Mr[ot] = vr;
+                Mi[ot] = vi;
             }
         }
 }

@@ -8,6 +8,7 @@
 #include <numeric>
 #include <set>
 
+#include "dfloat.cuh"
 #include "plan.h"
 
 namespace jk {
@@ -220,6 +221,9 @@ PlanDev Plan::dev() const
     d.compf = d_compf;
     d.ppi_pidx = d_ppi_pidx;
     d.phase = d_phase;
+    d.ppdf = d_ppdf;
+    d.gdf = d_gdf;
+    d.phasef = d_phasef;
     memcpy(d.L, L, sizeof L);
     memcpy(d.Finv, Finv, sizeof Finv);
     for (int i = 0; i < 9; ++i) {
@@ -321,6 +325,9 @@ static int alloc_ws(Plan *P)
             bytes += count * sizeof(int);
             return true;
         };
+        if (cudaMalloc((void **)&w.gtab2, std::max<size_t>(1, P->pvals.size()) * (size_t)gc * sizeof(float2)) != cudaSuccess)
+            return fail(JK_ERR_OOM, "cudaMalloc failed for the double-float Gaussian table");
+        bytes += std::max<size_t>(1, P->pvals.size()) * (size_t)gc * sizeof(float2);
         if (!alb(&w.Ms, 2 * (size_t)gc * sl) || !alb(&w.Zs, 2 * (size_t)gc * sl) || !alb(&w.Ds, sl) || !alb(&w.Cs, sl) ||
             !ali(&w.Mex, 2 * (size_t)gc * w.npad) || !ali(&w.Zex, 2 * (size_t)gc * w.npad) || !ali(&w.Dex, w.npad) ||
             !ali(&w.Cex, w.npad) || !ali(&w.eigIdx, w.npad) || !ali(&w.eigInfo, 1) || !al(&w.eigV, n2) || !al(&w.eigW, P->nbf) ||
@@ -863,6 +870,61 @@ int finish_plan_device(Plan *P)
         if ((rc = upload(P->pvals, &P->d_pvals, b)) || (rc = upload(P->ppi_pidx, &P->d_ppi_pidx, b)) || (rc = upload(gt0, &P->d_gtab0, b)) ||
             (rc = upload(ph, &P->d_phase, b)))
             return rc;
+        // double-float tables of the mixed-precision structure factors
+        std::vector<float4> phf(1024);
+        for (int k = 0; k < 1024; ++k) {
+            const long double t = 2.0L * 3.141592653589793238462643383279502884L * k / 1024.0L;
+            const long double c = std::cos(t), sn = std::sin(t);
+            const float ch = (float)c, sh = (float)sn;
+            phf[k] = make_float4(ch, (float)(c - ch), sh, (float)(sn - sh));
+        }
+        const int ng = (int)(P->gvec.size() / 4);
+        std::vector<float4> gd(3 * (size_t)std::max(ng, 1));
+        bool ok = true;
+        for (int g = 0; g < ng; ++g) {
+            const double *G = &P->gvec[4 * (size_t)g];
+            float nk[3];
+            for (int k = 0; k < 3; ++k) {
+                // n_k = a_k . G / 2 pi (an integer for a reciprocal-lattice vector)
+                const double v = (P->L[3 * k] * G[0] + P->L[3 * k + 1] * G[1] + P->L[3 * k + 2] * G[2]) / (2.0 * kPi);
+                const double r = std::rint(v);
+                if (std::fabs(v - r) > 1e-6 || std::fabs(r) > 64) ok = false;
+                nk[k] = (float)r;
+            }
+            const dfl gx = dfl_split(G[0]), gy = dfl_split(G[1]), gz = dfl_split(G[2]);
+            gd[3 * (size_t)g] = make_float4(nk[0], nk[1], nk[2], 0.0f);
+            gd[3 * (size_t)g + 1] = make_float4(gx.hi, gx.lo, gy.hi, gy.lo);
+            gd[3 * (size_t)g + 2] = make_float4(gz.hi, gz.lo, 0.0f, 0.0f);
+        }
+        std::vector<PpiDF> pd(std::max<size_t>(P->ppi.size(), 1));
+        for (size_t i = 0; i < P->ppi.size(); ++i) {
+            const PpiRec &x = P->ppi[i];
+            float f[3][3];
+            for (int k = 0; k < 3; ++k) {
+                const long double fk = (long double)P->Finv[3 * k] * x.P[0] + (long double)P->Finv[3 * k + 1] * x.P[1] +
+                                       (long double)P->Finv[3 * k + 2] * x.P[2];
+                frac_split3(fk, f[k]);
+            }
+            const dfl K = dfl_split(x.K), oo2p = dfl_split(0.5 / x.p);
+            dfl pa[3], pb[3];
+            for (int k = 0; k < 3; ++k) {
+                pa[k] = dfl_split(x.PA[k]);
+                pb[k] = dfl_split(x.PB[k]);
+            }
+            int pidx = P->ppi_pidx[i];
+            float pidx_bits;
+            memcpy(&pidx_bits, &pidx, sizeof pidx);
+            PpiDF &o = pd[i];
+            o.a = make_float4(f[0][0], f[1][0], f[2][0], K.hi);
+            o.b = make_float4(f[0][1], f[1][1], f[2][1], K.lo);
+            o.c = make_float4(f[0][2], f[1][2], f[2][2], pidx_bits);
+            o.d = make_float4(pa[0].hi, pa[0].lo, pa[1].hi, pa[1].lo);
+            o.e = make_float4(pa[2].hi, pa[2].lo, pb[0].hi, pb[0].lo);
+            o.f = make_float4(pb[1].hi, pb[1].lo, pb[2].hi, pb[2].lo);
+            o.g = make_float4(oo2p.hi, oo2p.lo, 0.0f, 0.0f);
+        }
+        P->sfac_df = ok;
+        if ((rc = upload(phf, &P->d_phasef, b)) || (rc = upload(gd, &P->d_gdf, b)) || (rc = upload(pd, &P->d_ppdf, b))) return rc;
     }
     std::vector<double> zeros((size_t)P->nbf * P->nbf, 0.0);
     if ((rc = upload(zeros, &P->d_S, b))) return rc;
@@ -878,7 +940,7 @@ void destroy_plan(Plan *P)
     if (!P) return;
     cudaSetDevice(P->device);
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
-                    P->d_g0, P->d_compf, P->d_ppi_ab, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->ws.gtab, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
+                    P->d_g0, P->d_compf, P->d_ppi_ab, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->d_ppdf, P->d_gdf, P->d_phasef, P->ws.gtab, P->ws.gtab2, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
                     P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
                     P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
                     P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};

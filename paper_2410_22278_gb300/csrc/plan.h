@@ -46,6 +46,7 @@ struct Workspace {
     unsigned cap = 0;
     int gc = 0;               // G vectors per chunk
     double *gtab = nullptr;   // [distinct p][gc]: (pi/p)^{3/2} e^{-G^2/4p} of the current G chunk
+    float2 *gtab2 = nullptr;  // the same as double-floats (mixed-precision structure factors)
     size_t bytes = 0;
     // split-precision tensor-core exchange (mixed precision)
     int npad = 0, oz_slices = 0;
@@ -131,6 +132,11 @@ struct Plan {
     double *d_pvals = nullptr, *d_gtab0 = nullptr;
     int *d_ppi_pidx = nullptr;
     double2 *d_phase = nullptr;
+    // double-float structure factors (mixed precision): usable when every
+    // reciprocal vector has |n_k| <= 64 in the reciprocal basis
+    bool sfac_df = false;
+    PpiDF *d_ppdf = nullptr;
+    float4 *d_gdf = nullptr, *d_phasef = nullptr;
     double *d_compf = nullptr;
     double *d_S = nullptr;  // raw-component overlap over the pair list
     size_t device_bytes = 0;
