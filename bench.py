@@ -438,8 +438,9 @@ def roofline(phases, real_flops, pk, pk_kind, sm_mhz_max):
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "ms": gemm_ms, "launches": gemm_n,
                     "peak_kind": "%s sustained bf16 (MEASURED_PEAKS.json)" % pk_kind, "work": "BF16 MMA flops issued"})
     sfac_ms, sfac_n = phases.get("recip_sfac", (0.0, 0))
-    out.append({"bound": "alu", "kernel": "k_sfac (structure factors)", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "ms": sfac_ms, "launches": sfac_n})
+    out.append({"bound": "alu", "kernel": "k_sfac_df (double-float structure factors)", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "ms": sfac_ms, "launches": sfac_n,
+                "traffic_note": "DRAM traffic of an earlier form of the kernel: profiles/sfac_df_water64.md"})
     out.sort(key=lambda r: -r["ms"])
     for r in out:
         r["ms_per_launch"] = r["ms"] / max(1, r["launches"])

@@ -145,7 +145,7 @@ static void launch_sfac_df(int cls, const PlanDev &pl, int sp0, int sp1, int g0,
 // (pi/p)^{3/2} e^{-G^2/4p} for every distinct pair exponent p and every G of
 // a chunk, laid out [p][g] (consecutive threads of the structure-factor
 // kernel read consecutive g); into tab (FP64) or, when tab2 is given, into
-// tab2 as double-floats
+// tab2 as double-floats times the weight sqrt(8 pi w(G) / V) of the G
 __global__ void k_gauss_table(int npv, const double *__restrict__ pv, const double *__restrict__ gv, int g0, int gcur,
                               double *__restrict__ tab, float2 *__restrict__ tab2)
 {
@@ -156,7 +156,7 @@ __global__ void k_gauss_table(int npv, const double *__restrict__ pv, const doub
     const double G2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2], p = pv[ip];
     const double v = (kPi / p) * sqrt(kPi / p) * exp(-G2 / (4.0 * p));
     if (tab2) {
-        const dfl d = dfl_split(v);
+        const dfl d = dfl_split(v * g[3]);
         tab2[e] = make_float2(d.hi, d.lo);
     } else {
         tab[e] = v;

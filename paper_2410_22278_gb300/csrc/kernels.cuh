@@ -898,6 +898,7 @@ __host__ __device__ __forceinline__ void sfac_df_poly(const dfl PA[3], const dfl
 // and Taylor series, the Gaussian factor from the chunk's double-float table,
 // the Hermite polynomials and the Cartesian products in double-float.
 // Relative accuracy about 1e-14 per term; the result is rounded to FP64.
+// gtab already carries the weight sqrt(8 pi w(G) / V).
 template <int LA, int LB>
 __global__ void __launch_bounds__(128) k_sfac_df(PlanDev pl, int sp0, int sp1, int g0, int gcur, const float2 *__restrict__ gtab,
                                                  double *__restrict__ M)
@@ -936,7 +937,7 @@ __global__ void __launch_bounds__(128) k_sfac_df(PlanDev pl, int sp0, int sp1, i
             dfl w, cs, sn;
             const int j = df_turns(gn.x, gn.y, gn.z, f1, f2, f3, w);
             df_sincos_turns(w, __ldg(pl.phasef + (j & 1023)), cs, sn);
-            // K (pi/p)^{3/2} e^{-G^2/4p} e^{-iG.P}
+            // K (pi/p)^{3/2} e^{-G^2/4p} sqrt(8 pi w(G) / V) e^{-iG.P}
             const float2 gt = __ldg(gtab + (size_t)__float_as_int(qc.w) * gcur + gi);
             const dfl amp = df_mul(dfl{qa.w, qb.w}, dfl{gt.x, gt.y});
             const dfl pr = df_mul(amp, cs), pim = df_neg(df_mul(amp, sn));
@@ -953,7 +954,6 @@ __global__ void __launch_bounds__(128) k_sfac_df(PlanDev pl, int sp0, int sp1, i
         }
     }
     const int n = pl.nbf;
-    const double sw = pl.gvec[4 * (g0 + gi) + 3];
     const int aoI = pl.shells[rec.I].ao, aoJ = pl.shells[rec.J].ao;
     double *Mr = M + (size_t)(2 * gi) * n * n;
     double *Mi = Mr + (size_t)n * n;
@@ -961,7 +961,9 @@ __global__ void __launch_bounds__(128) k_sfac_df(PlanDev pl, int sp0, int sp1, i
     for (int a = 0; a < NA; ++a)
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const double vr = sw * dfl_value(re[a * NB + b]), vi = sw * dfl_value(im[a * NB + b]);
+            // hi + lo in FP64, the conversions by integer operations (one FP64 add each)
+            const double vr = to_f64(re[a * NB + b].hi) + to_f64(re[a * NB + b].lo);
+            const double vi = to_f64(im[a * NB + b].hi) + to_f64(im[a * NB + b].lo);
             const size_t o = (size_t)(aoI + a) * n + aoJ + b;
             Mr[o] = vr;
             Mi[o] = vi;
