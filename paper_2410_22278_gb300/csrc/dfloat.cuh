@@ -18,8 +18,6 @@ struct dfl {
     float hi, lo;
 };
 
-__host__ __device__ __forceinline__ dfl dfl_of(float x) { return {x, 0.0f}; }
-
 // s + e = a + b exactly (any a, b)
 __host__ __device__ __forceinline__ dfl two_sum(float a, float b)
 {
