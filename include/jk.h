@@ -71,6 +71,12 @@ typedef struct {
     double mixed_switch;
 } jk_cutoffs;
 
+/* JK_FP64: every step in FP64.  JK_MIXED: real-space quartets split by
+ * mixed_switch (above); structure factors in double-float (pairs of FP32,
+ * about 44 bits; FP64 when a reciprocal vector has an integer coordinate
+ * beyond 64 in the reciprocal basis); the reciprocal exchange contraction
+ * as split-precision BF16 tensor-core GEMMs; accumulation, the reciprocal
+ * Coulomb contraction and the background in FP64. */
 typedef enum { JK_FP64 = 0, JK_MIXED = 1 } jk_precision;
 
 typedef struct jk_plan jk_plan; /* opaque; owns its device-resident pair and G data */
