@@ -324,8 +324,29 @@ def main():
     ej, ek = plan.energy(D.data_ptr(), J.data_ptr(), K.data_ptr(), st)
     if args.profile:
         print(json.dumps({"profile": args.workload, "ms_per_step": ms_per_step, "phases_ms": {k2: v for k2, v in phases.items()},
-                          "counts": counts}))
+                          "counts": counts, "counters": plan.counters(), "schedule": tiles}))
         return 0
+
+    # ---- errors of this build against the oracle's J and K rows of the same
+    # cell (tests/golden/water_rows_*.npz, written by tests/golden/make_rows.py
+    # from the oracle alone; the oracle used its own overlap for D, equal to
+    # the library's within 1e-14)
+    def vs_oracle(Jx, Kx):
+        import glob
+
+        if args.workload != "water64":
+            return None
+        dj = dk = 0.0
+        rows = 0
+        for f in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "water_rows_*.npz"))):
+            g = np.load(f)
+            r = g["rows"]
+            dj = max(dj, float(np.abs(Jx[r] - g["J"]).max()))
+            dk = max(dk, float(np.abs(Kx[r] - g["K"]).max()))
+            rows += len(r)
+        return {"max_abs_dJ": dj, "max_abs_dK": dk, "rows_compared": rows} if rows else None
+
+    mixed_vs_oracle = vs_oracle(Jm, Km)
 
     # ---- FP64 GPU form on the same GPU
     build(plan64)
@@ -341,6 +362,12 @@ def main():
     phases64 = plan64.build_times()
     J64, K64 = J.cpu().numpy(), K.cpu().numpy()
     ej64, ek64 = plan64.energy(D.data_ptr(), J.data_ptr(), K.data_ptr(), st)
+    fp64_vs_oracle = vs_oracle(J64, K64)
+    # FMA peaks of this GPU (the ALU roofline denominators), measured by the
+    # library's microbenchmark outside the timed region
+    fma_peaks = {"fp32_tflops": statistics.median(jk.microbench_fma(False) for _ in range(3)),
+                 "fp64_tflops": statistics.median(jk.microbench_fma(True) for _ in range(3)),
+                 "sms": torch.cuda.get_device_properties(dev).multi_processor_count}
 
     # ---- end to end through the C ABI with pinned host buffers
     Dp = torch.from_numpy(Dh).pin_memory()
@@ -361,7 +388,7 @@ def main():
     pk, pk_kind = peaks()
     launches = phases["total"][1]  # the library's own kernel launches per build (phases 0-5)
     nq = info["n_quartets_schwarz"]
-    roof, roof_other = roofline(phases, real_flops, pk, pk_kind, cl.get("sm_max_mhz") or 2070.0)
+    roof, roof_other = roofline(phases, real_flops, pk, pk_kind, fma_peaks)
     out = {
         "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -376,6 +403,9 @@ def main():
                  "phases_ms": {k2: v[0] for k2, v in phases64.items() if k2 != "mma_flops"}},
         "mixed_vs_fp64": {"max_abs_dJ": float(np.abs(Jm - J64).max()), "max_abs_dK": float(np.abs(Km - K64).max()),
                           "dE_Ha": (ej + ek) - (ej64 + ek64), "E_J": ej64, "E_K": ek64},
+        "mixed_vs_oracle_rows": mixed_vs_oracle,
+        "fp64_vs_oracle_rows": fp64_vs_oracle,
+        "fma_peaks_measured": fma_peaks,
         "phases_ms": {k2: v[0] for k2, v in phases.items() if k2 != "mma_flops"},
         "fp64_fraction": counts[0] / max(1, counts[0] + counts[1]),
         "autotuned_tiles": tiles,
@@ -396,40 +426,36 @@ def main():
     return 0
 
 
-FP32_LANES_PER_SM, N_SM = 128, 152
 # DRAM traffic of k_real<0,0,0,0,float> per launch on the 64-water box, from
-# ncu (dram__bytes_read.sum 28,487,168 + dram__bytes_write.sum 116,736)
-REAL_TILE_TRAFFIC = 28487168 + 116736
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (vector and tensor)
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass)
+REAL_TILE_TRAFFIC = None
 
 
-def roofline(phases, real_flops, pk, pk_kind, sm_mhz_max):
+def roofline(phases, real_flops, pk, pk_kind, fma):
     """Roofline of each kernel family of a mixed build, from the library's
     CUDA events on the build stream (phase sums over one build) and the work
     the kernels tallied: real-space FP32 tile kernels and FP64 list kernels
     (algorithmic flops of the McMurchie-Davidson steps, against the FP32 /
-    FP64 ALU peaks), split-precision GEMMs (BF16 MMA flops issued, against
-    the measured BF16 peak).  Returns the family with the most device time
-    first."""
+    FP64 FMA rates measured on this GPU by jk_microbench_fma), split-precision
+    GEMMs (BF16 MMA flops issued, against the measured BF16 peak).  Returns
+    the family with the most device time first."""
     fl64, fl32 = real_flops
     real_ms = phases["real_space"][0]
     list_ms, list_n = phases.get("real_fp64_list", (0.0, 0))
     tile_ms = max(real_ms - list_ms, 1e-9)
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    mk = "measured on this GPU (jk_microbench_fma: independent FMA chains, %d SMs, CUDA events)" % fma["sms"]
     out = [
         {"bound": "alu", "kernel": "k_real<..., float> (FP32 real-space quartet tiles)", "achieved": fl32 / (tile_ms / 1e3) / 1e12,
-         "peak": fp32_peak, "unit": "TFLOP/s", "frac": fl32 / (tile_ms / 1e3) / 1e12 / fp32_peak, "traffic": REAL_TILE_TRAFFIC,
-         "traffic_note": "DRAM bytes read + written by the largest launch of the family, k_real<0,0,0,0,float> on the 64-water box "
-                         "(ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass, profiles/real_ssss_fp32_water16.md)",
-         "ms": tile_ms, "launches": phases["real_space"][1] - list_n,
-         "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 flops x %.0f MHz" % (N_SM, FP32_LANES_PER_SM, sm_mhz_max),
+         "peak": fma["fp32_tflops"], "unit": "TFLOP/s", "frac": fl32 / (tile_ms / 1e3) / 1e12 / fma["fp32_tflops"],
+         "traffic": REAL_TILE_TRAFFIC, "ms": tile_ms, "launches": phases["real_space"][1] - list_n,
+         "peak_kind": "FP32 FMA rate " + mk,
          "work": "algorithmic flops of the MD steps (csrc/flops.h) tallied by the kernels"},
     ]
     if list_ms > 0:
         ach = fl64 / (list_ms / 1e3) / 1e12
-        out.append({"bound": "alu", "kernel": "k_real_list (FP64 large quartets)", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "ms": list_ms, "launches": list_n,
-                    "peak_kind": "nominal GB300 FP64", "work": "algorithmic flops of the MD steps (csrc/flops.h)"})
+        out.append({"bound": "alu", "kernel": "k_real_list (FP64 large quartets)", "achieved": ach, "peak": fma["fp64_tflops"],
+                    "unit": "TFLOP/s", "frac": ach / fma["fp64_tflops"], "traffic": None, "ms": list_ms, "launches": list_n,
+                    "peak_kind": "FP64 FMA rate " + mk, "work": "algorithmic flops of the MD steps (csrc/flops.h)"})
     gemm_ms, gemm_n = phases.get("tensor_gemm", (0.0, 0))
     if gemm_ms > 0:
         ach = phases["mma_flops"][0] / (gemm_ms / 1e3) / 1e12
@@ -437,10 +463,6 @@ def roofline(phases, real_flops, pk, pk_kind, sm_mhz_max):
         out.append({"bound": "tensor", "kernel": "k_ozaki_tc (split-precision BF16 tcgen05 GEMM)", "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "ms": gemm_ms, "launches": gemm_n,
                     "peak_kind": "%s sustained bf16 (MEASURED_PEAKS.json)" % pk_kind, "work": "BF16 MMA flops issued"})
-    sfac_ms, sfac_n = phases.get("recip_sfac", (0.0, 0))
-    out.append({"bound": "alu", "kernel": "k_sfac_df (double-float structure factors)", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "ms": sfac_ms, "launches": sfac_n,
-                "traffic_note": "DRAM traffic of an earlier form of the kernel: profiles/sfac_df_water64.md"})
     out.sort(key=lambda r: -r["ms"])
     for r in out:
         r["ms_per_launch"] = r["ms"] / max(1, r["launches"])

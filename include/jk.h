@@ -14,9 +14,13 @@
  * run lx descending, then ly descending (p: x y z; d: xx xy xz yy yz zz).
  * Matrices are nbf x nbf, row-major, FP64, symmetric.
  *
- * Threads: a plan is immutable after creation except for its build
- * workspace; jk_build calls on the same plan are serialised internally.
- * Distinct plans may be built concurrently on distinct streams.
+ * Threads: a plan is immutable after creation except for its one build
+ * workspace.  jk_build calls on the same plan, from any host threads and on
+ * any streams, are ordered one after another on the device: each call
+ * enqueues, under the plan's lock, a wait for the previous build on that plan
+ * before its own kernels, so two such builds never overlap on the workspace
+ * (the host is not blocked).  Distinct plans build concurrently on distinct
+ * streams.
  */
 #ifndef JK_H
 #define JK_H
@@ -32,7 +36,7 @@ extern "C" {
 #define JK_ERR_INVALID (-1)      /* bad argument: volume <= 0, exponent <= 0, nprim outside 1..16, NULL pointer */
 #define JK_ERR_UNSUPPORTED (-2)  /* angular momentum above 2 (d) */
 #define JK_ERR_OOM (-3)          /* device or host allocation failed, or the request exceeds a budget */
-#define JK_ERR_CUDA (-4)         /* a CUDA runtime or cuBLAS call failed */
+#define JK_ERR_CUDA (-4)         /* a CUDA runtime call or kernel launch failed */
 #define JK_ERR_TIMEOUT (-5)      /* a wait ran out of time (jk_wait, bounded device waits) */
 #define JK_ERR_DEVICE_CHECK (-6) /* a device-side bounds check tripped (an index outside its buffer) */
 #define JK_ERR_BUSY (-7)         /* no free slot / server shutting down */
@@ -75,8 +79,11 @@ typedef struct {
  * mixed_switch (above); structure factors in double-float (pairs of FP32,
  * about 44 bits; FP64 when a reciprocal vector has an integer coordinate
  * beyond 64 in the reciprocal basis); the reciprocal exchange contraction
- * as split-precision BF16 tensor-core GEMMs; accumulation, the reciprocal
- * Coulomb contraction and the background in FP64. */
+ * as split-precision BF16 tensor-core GEMMs, in a low-rank form when the
+ * device-side factorisation of D finds a rank within 60% of nbf (a
+ * closed-shell density has rank n_occ), else in the dense form;
+ * accumulation, the reciprocal Coulomb contraction and the background in
+ * FP64. */
 typedef enum { JK_FP64 = 0, JK_MIXED = 1 } jk_precision;
 
 typedef struct jk_plan jk_plan; /* opaque; owns its device-resident pair and G data */
@@ -122,6 +129,19 @@ int jk_plan_info(const jk_plan *plan, jk_plan_stats *out);
 int jk_pair_counts(const jk_cell *cell, const jk_shell *shells, int nshell, double omega, const jk_cutoffs *cut,
                    long long counts[5]);
 
+/* Keep the plan's D-independent reciprocal-space data resident between
+ * builds (no counterpart in the paper, which recomputes its reciprocal
+ * terms per quartet): the pair structure factors of every reciprocal vector
+ * (2 n_G nbf^2 FP64) and, for JK_MIXED plans, their BF16 exchange slices.
+ * The next jk_build fills the cache; later builds skip the structure
+ * factors and their slicing, which for an SCF loop or repeated frames of
+ * one geometry are the same every build.  Allocated at once if the total
+ * fits max_bytes, else JK_ERR_OOM (the plan then works as before);
+ * max_bytes = 0 releases it.  *bytes (may be NULL) receives the size.
+ * Waits for the plan's last build.  jk_plan_info's device_bytes includes
+ * the cache. */
+int jk_plan_cache(jk_plan *plan, size_t max_bytes, size_t *bytes);
+
 /* Number of basis functions of the plan (or -1 for NULL). */
 int jk_plan_nbf(const jk_plan *plan);
 
@@ -138,7 +158,9 @@ void jk_plan_destroy(jk_plan *plan);
  * device.  D must be symmetric; J and K are overwritten and come out
  * symmetric; either may be NULL to skip it (K is the expensive one).
  * Stream-ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default);
- * returns after enqueueing.  Caller keeps ownership of D, J, K. */
+ * returns after enqueueing and never waits for the device (every decision
+ * that depends on D -- the mixed-precision split, the rank of D -- is taken
+ * on the device).  Caller keeps ownership of D, J, K. */
 int jk_build(jk_plan *plan, const double *D, double *J, double *K, void *cuda_stream);
 
 /* Same as jk_build with HOST buffers (row-major FP64): copies D in, builds,
@@ -191,26 +213,48 @@ int jk_energy_noalloc(const jk_plan *plan, const double *D, const double *J, con
  * phase.  n = number of slots the caller provides (<= 11 used). */
 int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
 
-/* Autotuner (no counterpart in the paper): choose the tile shape (kets
- * per tile) of every real-space class-pair kernel by timing candidates
- * {8, 16, 32, 64, 128} on a sub-range of bras with CUDA events, on
+/* Autotuner (no counterpart in the paper): choose the tile shape of every
+ * real-space class-pair kernel (kets per warp, candidates 128 .. 2048, for
+ * the warp kernels of the s and p classes; kets per tile, 8 .. 128, for the
+ * classes with a d shell) by timing the candidates on a sub-range of bras
+ * with CUDA events, on
  * `cuda_stream`, using density D (device, as in jk_build) for realistic
  * work.  If cache_path is not NULL, choices are read from and written to
  * that text file, keyed by GPU name, precision, class pair and size
- * bucket.  chosen (may be NULL) receives up to 21 choices in class-pair
- * order.  Overwrites the plan's build workspace; synchronises the stream. */
+ * bucket.  chosen (may be NULL) receives 42 ints: (family, kets) for each
+ * of the 21 class pairs (bra class <= ket class, classes ss, ps, pp, ds,
+ * dp, dd), family 0 lane-per-bra, 1 warp.  Overwrites the plan's build
+ * workspace; synchronises the stream. */
 int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *cache_path, int *chosen);
+
+/* Set the real-space schedule directly (what jk_autotune chooses): sched
+ * holds (family, kets) for the first n class pairs in jk_autotune's order;
+ * family 1 (warp kernels) only for class pairs of s and p shells, kets in
+ * 1..65535.  Results do not depend on the schedule beyond rounding.
+ * Errors: JK_ERR_INVALID (nothing is changed). */
+int jk_plan_set_schedule(jk_plan *plan, const int *sched, int n);
 
 /* Work counters of the most recent jk_build (waits for it to finish):
  * counts[0] unique image quartets evaluated in real space in FP64,
  * counts[1] those evaluated in FP32 (mixed precision only), counts[2]
  * quartets that the mixed policy wanted in FP64 but that overflowed the
  * plan's FP64 list and were evaluated in FP32 (0 in a healthy build),
- * counts[3] 0, counts[4] and counts[5] the algorithmic floating-point
- * operations of the real-space evaluation in FP64 and in FP32 (operation
- * counts of the McMurchie-Davidson steps per evaluated lattice image,
- * primitive quartet and image quartet).  n <= 6.  Returns JK_ERR_TIMEOUT
- * (and the build's J and K are NaN) if a bounded device wait ran out. */
+ * counts[3] the number of pivots of the density factorisation of a mixed
+ * build with K (the numerical rank of D' when counts[6] is 1),
+ * counts[4] and counts[5] the algorithmic floating-point operations of the
+ * real-space evaluation in FP64 and in FP32 (the McMurchie-Davidson steps:
+ * ket Hermite coefficients per bra image and ket primitive, seeds and R
+ * table per lattice image inside the screening sphere, prefactor and
+ * Hermite contraction per primitive quartet, digestion per image quartet;
+ * a transcendental counts one, a fused multiply-add two),
+ * counts[6] 1 if the reciprocal exchange took the low-rank form, else 0,
+ * counts[7] and counts[8] the screening and bookkeeping operations in FP64
+ * and FP32 (radii, minimum images, image search, recomputed bra
+ * coefficients), counts[9] and counts[10] the lane-terms processed and the
+ * lane slots offered by the FP64 primitive loops (their ratio is the lane
+ * occupancy), counts[11] and counts[12] the same for FP32.  n <= 13.
+ * Returns JK_ERR_TIMEOUT (and the build's J and K are NaN) if a bounded
+ * device wait ran out. */
 int jk_build_counts(jk_plan *plan, long long *counts, int n);
 
 /* Gamma overlap over the plan's pair list (Eq. pbc_overlap_formula),

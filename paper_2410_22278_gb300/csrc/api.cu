@@ -119,7 +119,7 @@ int jk_plan_info(const jk_plan *plan, jk_plan_stats *o)
     o->g_max = P->g_max;
     o->r1_max = P->r1_max;
     o->volume = P->volume;
-    o->device_bytes = P->device_bytes;
+    o->device_bytes = P->device_bytes + P->cache.bytes;
     o->workspace_bytes = P->ws.bytes;
     return JK_OK;
 }
@@ -143,9 +143,30 @@ int jk_build(jk_plan *plan, const double *D, double *J, double *K, void *cuda_st
     try {
         cudaStream_t st = (cudaStream_t)cuda_stream;
         if (cudaSetDevice(plan->p->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+        // one critical section: order after the previous build on this plan,
+        // enqueue, and publish this build's completion event, so builds from
+        // several host threads on several streams run one after another on
+        // the plan's single workspace
+        std::lock_guard<std::mutex> g(plan->p->build_mu);
         cudaStreamWaitEvent(st, plan->done, 0);
         int rc = jk::run_build(plan->p, D, J, K, st);
         cudaEventRecord(plan->done, st);
+        return rc;
+    } catch (...) {
+        return fail(JK_ERR_INVALID, "unexpected host exception");
+    }
+}
+
+int jk_plan_cache(jk_plan *plan, size_t max_bytes, size_t *bytes)
+{
+    if (!plan) return fail(JK_ERR_INVALID, "plan is NULL");
+    try {
+        if (cudaSetDevice(plan->p->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+        std::lock_guard<std::mutex> g(plan->p->build_mu);
+        // the cache may be in use by the plan's last build
+        if (cudaEventSynchronize(plan->done) != cudaSuccess) return fail(JK_ERR_CUDA, "previous build failed");
+        int rc = jk::cache_reciprocal(plan->p, max_bytes);
+        if (bytes) *bytes = plan->p->cache.bytes;
         return rc;
     } catch (...) {
         return fail(JK_ERR_INVALID, "unexpected host exception");
@@ -164,6 +185,8 @@ int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *c
     if (!plan || !D) return fail(JK_ERR_INVALID, "plan or D is NULL");
     try {
         cudaStream_t st = (cudaStream_t)cuda_stream;
+        if (cudaSetDevice(plan->p->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+        std::lock_guard<std::mutex> g(plan->p->build_mu);
         cudaStreamWaitEvent(st, plan->done, 0);
         int rc = jk::autotune(plan->p, D, st, cache_path, chosen);
         cudaEventRecord(plan->done, st);
@@ -171,6 +194,13 @@ int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *c
     } catch (...) {
         return fail(JK_ERR_INVALID, "unexpected host exception");
     }
+}
+
+int jk_plan_set_schedule(jk_plan *plan, const int *sched, int n)
+{
+    if (!plan || !sched || n < 0 || n > 21) return fail(JK_ERR_INVALID, "bad schedule arguments");
+    std::lock_guard<std::mutex> g(plan->p->build_mu);
+    return jk::set_schedule(plan->p, sched, n);
 }
 
 int jk_build_counts(jk_plan *plan, long long *counts, int n)

@@ -217,25 +217,19 @@ void PhaseTimer::destroy()
     pool.clear();
 }
 
-#define BLAS_OK(x)                                                                       \
-    do {                                                                                 \
-        if ((x) != CUBLAS_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cuBLAS call failed: " #x); \
-    } while (0)
-
+// The caller holds P->build_mu (jk_build), so the stream ordering against
+// the previous build on this plan and the use of its workspace are one
+// critical section.
 int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
 {
-    std::lock_guard<std::mutex> guard(P->build_mu);
     if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
     const int n = P->nbf;
     const size_t n2 = (size_t)n * n;
     PlanDev pl = P->dev();
     Workspace &w = P->ws;
-    BLAS_OK(cublasSetStream(P->blas, st));
-    BLAS_OK(cublasSetPointerMode(P->blas, CUBLAS_POINTER_MODE_HOST));
     const bool mixed = P->precision == JK_MIXED;
     PhaseTimer &tm = P->timer;
     tm.begin(st);
-    w.mma_flops = 0;
     const int ev_all = tm.start(6);
     int ev = tm.start(0);
 
@@ -251,15 +245,14 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     cudaMemsetAsync(w.JLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.KLR, 0, n2 * sizeof(double), st);
     cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), st);
-    cudaMemsetAsync(w.cnt, 0, 8 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(w.cnt, 0, kCounters * sizeof(unsigned long long), st);
     if (w.nbig) cudaMemsetAsync(w.nbig, 0, 2 * sizeof(unsigned), st);
     int rc;
     if ((rc = cuda_check("prologue"))) return rc;
-    // mixed precision: slices of D' and the eigendecomposition of D' for the
-    // exchange contraction, enqueued now so they overlap nothing and are
-    // ready when the reciprocal phase needs them
+    // mixed precision: slices of D' and its low-rank factorisation for the
+    // exchange contraction (decided on the device; nothing waits for it)
     if (mixed && K && (rc = ozaki_begin(P, st))) return rc;
-    tm.stop(0, ev, mixed ? 4 : 1);
+    tm.stop(0, ev, mixed ? (K ? 8 : 4) : 1);
 
     // ---- real space
     ev = tm.start(1);
@@ -276,6 +269,7 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             a.k1 = Kc.b1;
             a.same = cb == ck;
             a.kchunk = P->kchunk[cb][ck];
+            a.variant = P->kvariant[cb][ck];
             a.tau = P->mixed_tau;
             a.Dp = w.Dp;
             a.dmax = w.dmax;
@@ -318,52 +312,60 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     const int ng = (int)(P->gvec.size() / 4);
     // mixed precision: structure factors in double-float on the FP32 pipe
     const bool sfac_df = mixed && P->sfac_df && w.gtab2;
-    if (mixed && K && (rc = ozaki_prepare_lowrank(P, st))) return rc;
-    for (int g0 = 0; g0 < ng; g0 += w.gc) {
+    // the D-independent structure factors (and their exchange slices) come
+    // from the reciprocal cache once a build has filled it
+    RecipCache &cache = P->cache;
+    const bool fill_cache = cache.on && !cache.valid;
+    for (int g0 = 0, chunk = 0; g0 < ng; g0 += w.gc, ++chunk) {
         const int gcur = std::min(w.gc, ng - g0);
-        ev = tm.start(2);
-        int nsf = 0;
-        {
+        double *Mc = cache.on ? cache.M + 2 * (size_t)g0 * n2 : w.M;
+        if (!cache.on || fill_cache) {
+            ev = tm.start(2);
+            int nsf = 0;
             const long long ne = (long long)P->pvals.size() * gcur;
             k_gauss_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>((int)P->pvals.size(), P->d_pvals, P->d_gvec, g0, gcur, w.gtab,
                                                                          sfac_df ? w.gtab2 : nullptr);
+            for (int c = 0; c < JK_NCLASS_MAX; ++c) {
+                if (sfac_df)
+                    launch_sfac_df(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], g0, gcur, w.gtab2, Mc, st);
+                else
+                    launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, Mc, st);
+                nsf += P->spair_class_off[c + 1] > P->spair_class_off[c];
+            }
+            if ((rc = cuda_check("structure factors"))) return rc;
+            tm.stop(2, ev, nsf + 1);
         }
-        for (int c = 0; c < JK_NCLASS_MAX; ++c) {
-            if (sfac_df)
-                launch_sfac_df(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], g0, gcur, w.gtab2, w.M, st);
-            else
-                launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, w.M, st);
-            nsf += P->spair_class_off[c + 1] > P->spair_class_off[c];
-        }
-        if ((rc = cuda_check("structure factors"))) return rc;
-        tm.stop(2, ev, nsf);
-        const double one = 1.0, zero = 0.0;
         const int m2 = 2 * gcur;
         if (J) {
+            // rho_D = M^T vec(D'), J_LR += M rho_D (two passes over the slab)
             ev = tm.start(3);
-            BLAS_OK(cublasDgemv(P->blas, CUBLAS_OP_T, (int)n2, m2, &one, w.M, (int)n2, w.Dp, 1, &zero, w.rho, 1));
-            BLAS_OK(cublasDgemv(P->blas, CUBLAS_OP_N, (int)n2, m2, &one, w.M, (int)n2, w.rho, 1, &one, w.JLR, 1));
-            tm.stop(3, ev, 2);
+            slab_gemv_t(Mc, (long long)n2, m2, w.Dp, w.rho_part, w.rho, st);
+            slab_gemv_n(Mc, (long long)n2, m2, w.rho, 1.0, w.JLR, st);
+            tm.stop(3, ev, 3);
         }
         if (K) {
             ev = tm.start(4);
             if (mixed) {
                 // split-precision BF16 tensor-core GEMMs, slices per chunk from its G bound
-                if ((rc = ozaki_exchange_chunk(P, m2, w.chunk_slices[g0 / w.gc], st))) return rc;
+                if ((rc = ozaki_exchange_chunk(P, chunk, Mc, m2, w.chunk_slices[chunk], st))) return rc;
                 tm.stop(4, ev, 4);
             } else {
-                // the plain FP64 form: K_LR += [M_1 .. M_2g] [Z_1; ..; Z_2g], Z_b = D' M_b (native DGEMM)
-                BLAS_OK(cublasDgemmStridedBatched(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, w.Dp, n, 0, w.M, n, (long long)n2,
-                                                  &zero, w.Z, m2 * n, n, m2));
-                BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, m2 * n, &one, w.M, n, w.Z, m2 * n, &one, w.KLR, n));
+                // the plain FP64 form: Z_b = D' M_b, then K_LR += sum_b M_b Z_b
+                // (upper tiles; the product is symmetric), FP64 GEMMs
+                dgemm_batched(n, n, n, w.Dp, n, 0, Mc, n, (long long)n2, w.Z, n, (long long)n2, m2, 1.0, 0.0, false, st);
+                dgemm_batched(n, n, n, Mc, n, (long long)n2, w.Z, n, (long long)n2, w.KLR, n, 0, m2, 1.0, 0.0, true, st);
                 tm.stop(4, ev, 2);
             }
         }
     }
+    // filled in stream order: later builds on this plan are ordered after this one
+    if (fill_cache && (!mixed || K)) cache.valid = true;
     if (mixed && K) {
         ev = tm.start(4);
         if ((rc = ozaki_finish(P, st))) return rc;
         tm.stop(4, ev, 1);
+    } else if (K && ng > 0) {
+        mirror_upper(n, w.KLR, st);
     }
     ev = tm.start(5);
 
@@ -371,9 +373,9 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     const double cbg = -kPi / (P->volume * P->omega * P->omega);
     k_dot2<<<grid_for(n2), 256, 0, st>>>(n2, P->d_S, w.Dp, nullptr, w.scal);
     if (K) {
-        const double one = 1.0, zero = 0.0;
-        BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, w.Dp, n, P->d_S, n, &zero, w.T1, n));
-        BLAS_OK(cublasDgemm(P->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, P->d_S, n, w.T1, n, &zero, w.T2, n));
+        // S D' S (both factors symmetric; FP64 GEMMs)
+        dgemm_batched(n, n, n, w.Dp, n, 0, P->d_S, n, 0, w.T1, n, (long long)n2, 1, 1.0, 0.0, false, st);
+        dgemm_batched(n, n, n, P->d_S, n, 0, w.T1, n, 0, w.T2, n, (long long)n2, 1, 1.0, 0.0, false, st);
     }
     k_final<<<grid_for(n2), 256, 0, st>>>(n, P->d_compf, w.X, w.Y, w.JLR, w.KLR, P->d_S, w.T2, w.scal, cbg, w.err, J, K);
     tm.stop(5, ev, K ? 4 : 2);
@@ -388,7 +390,6 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
 // precision, class pair and size bucket) when cache_path is given.
 int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, int *chosen)
 {
-    std::lock_guard<std::mutex> guard(P->build_mu);
     if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, P->device);
@@ -414,15 +415,24 @@ int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cands[] = {8, 16, 32, 64, 128};
+    float part_ms = 0;
+    // candidates (family, kets per tile): lane-per-bra kernels with 8 .. 128
+    // kets per tile, and for s and p class pairs the warp kernels with
+    // 128 .. 2048 kets per warp; a choice is stored as family * 65536 + kets
+    std::vector<int> cands_t = {8, 16, 32, 64, 128}, cands_w;
+    for (int c : {128, 256, 512, 1024, 2048}) cands_w.push_back(65536 + c);
     int k = 0;
     bool dirty = false;
     for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
-        for (int ck = cb; ck < JK_NCLASS_MAX; ++ck) {
+        for (int ck = cb; ck < JK_NCLASS_MAX; ++ck, ++k) {
             const ClassRange &B = P->classes[cb], &Kc = P->classes[ck];
+            if (chosen) {
+                chosen[2 * k] = P->kvariant[cb][ck];
+                chosen[2 * k + 1] = P->kchunk[cb][ck];
+            }
             if (B.b1 <= B.b0 || Kc.b1 <= Kc.b0) continue;
             char key[512];
-            snprintf(key, sizeof key, "%s|%s|%d%d|%d|%d", prop.name, mixed ? "mixed" : "fp64", cb, ck, bucket(B.b1 - B.b0),
+            snprintf(key, sizeof key, "%s|%s|v2|%d%d|%d|%d", prop.name, mixed ? "mixed" : "fp64", cb, ck, bucket(B.b1 - B.b0),
                      bucket(Kc.b1 - Kc.b0));
             for (char *q = key; *q; ++q)
                 if (*q == ' ') *q = '_';
@@ -432,46 +442,61 @@ int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, 
                 best = it->second;
             } else {
                 float best_ms = 1e30f;
-                for (int c : cands) {
-                    RealLaunch a{};
-                    a.pl = pl;
-                    a.b0 = B.b0;
-                    a.b1 = std::min(B.b1, B.b0 + 4096);
-                    a.k0 = Kc.b0;
-                    a.k1 = Kc.b1;
-                    a.same = cb == ck;
-                    a.kchunk = c;
-                    a.mode = 0;
-                    a.fp32 = mixed;
-                    a.Dp = w.Dp;
-                    a.dmax = w.dmax;
-                    a.Dpf = w.Dpf;
-                    a.dmaxf = w.dmaxf;
-                    a.X = w.X;
-                    a.Y = w.Y;
-                    a.cnt = w.cnt;
-                    a.st = st;
-                    cudaEventRecord(e0, st);
-                    launch_real(cb, ck, a);
-                    cudaEventRecord(e1, st);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        cudaEventDestroy(e0);
-                        cudaEventDestroy(e1);
-                        return fail(JK_ERR_CUDA, "autotune launch failed");
+                std::vector<int> cands = cands_t;
+                if (real_has_warp_kernel(cb, ck)) cands.insert(cands.end(), cands_w.begin(), cands_w.end());
+                // two sub-ranges of at most 2048 bras (the class is sorted by
+                // primitive count, so the start and the middle differ)
+                const int nbc = B.b1 - B.b0, mid = B.b0 + nbc / 2;
+                for (int c : cands)
+                    for (int part = 0; part < 2; ++part) {
+                        RealLaunch a{};
+                        a.pl = pl;
+                        a.b0 = part == 0 ? B.b0 : std::max(B.b0 + std::min(nbc, 2048), mid);
+                        a.b1 = std::min(B.b1, a.b0 + 2048);
+                        if (a.b1 <= a.b0) continue;
+                        a.k0 = Kc.b0;
+                        a.k1 = Kc.b1;
+                        a.same = cb == ck;
+                        a.kchunk = c & 65535;
+                        a.variant = c >> 16;
+                        a.mode = 0;
+                        a.fp32 = mixed;
+                        a.Dp = w.Dp;
+                        a.dmax = w.dmax;
+                        a.Dpf = w.Dpf;
+                        a.dmaxf = w.dmaxf;
+                        a.X = w.X;
+                        a.Y = w.Y;
+                        a.cnt = w.cnt;
+                        a.st = st;
+                        cudaEventRecord(e0, st);
+                        launch_real(cb, ck, a);
+                        cudaEventRecord(e1, st);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) {
+                            cudaEventDestroy(e0);
+                            cudaEventDestroy(e1);
+                            return fail(JK_ERR_CUDA, "autotune launch failed");
                     }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        best = c;
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (part == 0) part_ms = ms;
+                        else part_ms += ms;
+                        if (part == 1 || nbc <= 2048) {
+                            if (part_ms < best_ms) {
+                                best_ms = part_ms;
+                                best = c;
+                            }
                     }
                 }
                 cache[key] = best;
                 dirty = true;
             }
-            P->kchunk[cb][ck] = best;
-            if (chosen && k < 36) chosen[k] = best;
-            ++k;
+            P->kchunk[cb][ck] = best & 65535;
+            P->kvariant[cb][ck] = best >> 16;
+            if (chosen) {
+                chosen[2 * k] = best >> 16;
+                chosen[2 * k + 1] = best & 65535;
+            }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -486,18 +511,44 @@ int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, 
     return cuda_check("autotune");
 }
 
+// Real-space schedule given by the caller: (family, kets per tile) per
+// class pair in the order of jk_autotune's output.
+int set_schedule(Plan *P, const int *sched, int n)
+{
+    int k = 0;
+    for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
+        for (int ck = cb; ck < JK_NCLASS_MAX; ++ck, ++k) {
+            if (k >= n) return JK_OK;
+            const int fam = sched[2 * k], kets = sched[2 * k + 1];
+            if (fam < 0 || fam > 1 || (fam == 1 && !real_has_warp_kernel(cb, ck)) || kets < 1 || kets > 65535)
+                return fail(JK_ERR_INVALID, "schedule entry " + std::to_string(k) + " out of range");
+        }
+    k = 0;
+    for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
+        for (int ck = cb; ck < JK_NCLASS_MAX && k < n; ++ck, ++k) {
+            P->kvariant[cb][ck] = sched[2 * k];
+            P->kchunk[cb][ck] = sched[2 * k + 1];
+        }
+    return JK_OK;
+}
+
 int build_counts(Plan *P, long long *counts, int n)
 {
-    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long h[kCounters] = {};
     unsigned hb[2] = {0, 0};
     if (P->timer.next > 0 && cudaEventSynchronize(P->timer.pool[P->timer.next - 1]) != cudaSuccess)
         return fail(JK_ERR_CUDA, "build did not finish");
     if (cudaMemcpy(h, P->ws.cnt, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(JK_ERR_CUDA, "count copy failed");
     if (P->ws.nbig && cudaMemcpy(hb, P->ws.nbig, sizeof hb, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(JK_ERR_CUDA, "count copy failed");
-    h[2] = hb[1];
-    h[3] = 0;
-    for (int i = 0; i < n && i < 6; ++i) counts[i] = (long long)h[i];
+    // rank and form of the density factorisation (mixed builds with K)
+    int dyn[4] = {0, 0, 0, 0};
+    if (P->precision == JK_MIXED && P->ws.lr.dyn && cudaMemcpy(dyn, P->ws.lr.dyn, sizeof dyn, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(JK_ERR_CUDA, "status copy failed");
+    // public layout (jk_build_counts)
+    const long long out[13] = {(long long)h[0], (long long)h[1], (long long)hb[1], dyn[3], (long long)h[4], (long long)h[5], dyn[0],
+                               (long long)h[8], (long long)h[9], (long long)h[12], (long long)h[14], (long long)h[13], (long long)h[15]};
+    for (int i = 0; i < n && i < 13; ++i) counts[i] = out[i];
     unsigned e = 0;
     if (cudaMemcpy(&e, P->ws.err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(JK_ERR_CUDA, "check word copy failed");
     if (e) return fail(JK_ERR_TIMEOUT, "a bounded wait in a tensor-core GEMM ran out; J and K of that build are NaN");
@@ -523,7 +574,15 @@ int build_times(Plan *P, double *ms, int *launches, int n)
     int tot = 0;
     for (int i = 0; i < 6; ++i) tot += tm.launches[i];
     if (launches && n > 6) launches[6] = tot;
-    if (ms && n > 10) ms[10] = P->ws.mma_flops;  // slot 10: BF16 MMA flops issued (for the tensor roofline)
+    if (ms && n > 10) {
+        // slot 10: BF16 MMA flops issued (for the tensor roofline), from the
+        // form and rank the device chose
+        int dyn[3] = {0, 0, 0};
+        if (P->precision == JK_MIXED && P->ws.lr.dyn &&
+            cudaMemcpy(dyn, P->ws.lr.dyn, sizeof dyn, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(JK_ERR_CUDA, "status copy failed");
+        ms[10] = P->precision == JK_MIXED ? ozaki_mma_flops(P, dyn) : 0.0;
+    }
     return JK_OK;
 }
 

@@ -8,7 +8,7 @@
 //     angular class (l_I, l_J) and sorted by descending Schwarz estimate;
 //   * local primitive pairs (the bottom layer): P, P-A, P-B(R), p and the
 //     prefactor K = c_a c_b exp(-ab/p |A-B-R|^2) (Eq. E_recursion_0 folded
-//     into K), sorted by |K| inside each image;
+//     into K), sorted inside each image by descending B = |K| p^{-5/4};
 //   * the Boys-function Taylor table, the R1 candidate lattice vectors for
 //     the real-space sums and the half-space reciprocal vectors.
 #pragma once
@@ -93,6 +93,8 @@ struct PlanDev {
     const double *boys;          // [JK_BOYS_NPTS][JK_BOYS_MCOL]
     const float *boys_f;
     const PpiF *ppf;
+    const float *ppB;            // B = |K| p^{-5/4} of each primitive pair (descending inside an image)
+    float mag_thr;               // B_i B_j below this: the primitive quartet is below the real-space threshold
     const double *r1;            // [nr1][4]: x, y, z, |R|, sorted by |R|
     const float *r1f;            // the same in single precision
     int nr1;

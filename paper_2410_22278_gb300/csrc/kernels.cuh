@@ -168,7 +168,12 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
     // rolled: full unrolling there only bloats code and compile time
     constexpr int UNR = L >= 6 ? 1 : 64;
     const float iw2 = pl.inv_omega2f;
+    // primitive pairs are in descending order of B = |K| p^{-5/4}: the loops
+    // end at the first pair whose bound B_i B_j falls below the threshold
+    const float Bk0 = __ldg(pl.ppB + sk.pp0);
     for (int i = 0; i < sb.npp; ++i) {
+        const float Bi = __ldg(pl.ppB + sb.pp0 + i);
+        if (Bi * Bk0 < pl.mag_thr) break;
         const PpiF xf = pl.ppf[sb.pp0 + i];
         PairT<T> x;
         load_pair(pl, sb.pp0 + i, xf, x);
@@ -178,6 +183,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
 #pragma unroll
         for (int k = 0; k < 3; ++k) herm_E<LA, LB, T>(x.PA[k], x.PB[k], oo2p, Ea[k]);
         for (int j = 0; j < sk.npp; ++j) {
+            if (Bi * __ldg(pl.ppB + sk.pp0 + j) < pl.mag_thr) break;
             const PpiF yf = pl.ppf[sk.pp0 + j];
             // ---- screening, single precision
             const float ipf = xf.pad, iqf = yf.pad;

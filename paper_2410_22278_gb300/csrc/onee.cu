@@ -15,7 +15,6 @@
 //                structure-factor slab as the Coulomb build, contracted with
 //                the nuclear structure factor by one matrix-vector product;
 //   self term    +(pi / (V w^2)) Z_tot S_ab (Eq. v1e_self_term).
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -322,16 +321,13 @@ int one_electron(Plan *P, int natom, const double *Z, const double *xyz, double 
         launch_onee(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], 1, P->d_ppi_ab, natom, dZ, dX, dC, ncand, w.T2, st);
     // reciprocal part, chunk by chunk of G
     const int ng = (int)(P->gvec.size() / 4);
-    const double minus_one = -1.0, one = 1.0;
     for (int g0 = 0; g0 < ng; g0 += w.gc) {
         const int gcur = std::min(w.gc, ng - g0);
         launch_gauss_table(P, g0, gcur, w.gtab, st);
         for (int c = 0; c < JK_NCLASS_MAX; ++c)
             launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, w.M, st);
         k_nuclear_sfac<<<(gcur + 127) / 128, 128, 0, st>>>(natom, dZ, dX, P->d_gvec, g0, gcur, dn);
-        if (cublasSetStream(P->blas, st) != CUBLAS_STATUS_SUCCESS ||
-            cublasDgemv(P->blas, CUBLAS_OP_N, (int)n2, 2 * gcur, &minus_one, w.M, (int)n2, dn, 1, &one, w.T2, 1) != CUBLAS_STATUS_SUCCESS)
-            return fail(JK_ERR_CUDA, "cuBLAS failed in the nuclear attraction");
+        slab_gemv_n(w.M, (long long)n2, 2 * gcur, dn, -1.0, w.T2, st);
     }
     // self term +(pi/(V w^2)) Z_tot S and the component factors
     k_onee_final<<<grid, 256, 0, st>>>(n, P->d_compf, w.T2, P->d_S, kPi / (P->volume * w2) * ztot, V);

@@ -20,19 +20,22 @@
 //
 // Two factorisations of the contraction:
 //   dense:    Zt_b = (D M_b)^T, then K += sum_b M_b Z_b;
-//   low rank: D = C+ C+^T - C- C-^T from the eigenvalues of D kept above a
-//             relative 1e-10 (a closed-shell SCF density has rank n_occ), then
+//   low rank: D = C+ C+^T - C- C-^T from the device-side pivoted LDL^T of
+//             dense.cu (a closed-shell SCF density has rank n_occ), then
 //             Y_b = M_b [C+ C-] and K += sum_b Y+_b Y+_b^T - Y-_b Y-_b^T.
+// Which form a build takes is decided on the device: the launches of both
+// are enqueued, and each kernel reads the factorisation's status array
+// (TcArgs::dyn) and returns at once when its form was not chosen.
 // M_b is symmetric, so its row slices serve as the A operand of one GEMM
 // and the B operand (B^T rows) of the other; the K GEMMs form only tiles on
 // or above the diagonal and mirror them.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "plan.h"
@@ -115,8 +118,9 @@ __global__ void k_ozaki_slice(const double *__restrict__ X, int rows, int cols, 
 // (hi, lo) float pairs (read by the pair slicer), MODE 1 adds them into
 // float-pair partial sums with FP32 two-sums.
 struct TcArgs {
-    int a_batch_rows, a_slice_rows;  // TMA row of A slice s, batch b: b*a_batch_rows + s*a_slice_rows + row
+    int a_batch_rows, a_slice_rows;  // TMA row of A slice s, batch b: a_row0 + b*a_batch_rows + s*a_slice_rows + row
     int b_batch_rows, b_slice_rows;
+    int a_row0, b_row0;              // first row of the operand in its tensor map (a chunk of the reciprocal cache)
     const int *Aex;
     int a_exb;  // exponents of batch b at Aex[b * a_exb] (a_exb = 0: shared)
     const int *Bex;
@@ -132,6 +136,13 @@ struct TcArgs {
     int ldp;
     float sign;
     unsigned *err;
+    // device status of the low-rank factorisation (dyn[0] low rank chosen,
+    // dyn[1] rows of C+, dyn[2] rows of C-) and what this launch computes:
+    // 0 always, 1 dense form only, 2 Y = M [C+ C-] (column tiles up to
+    // dyn[1] + dyn[2]), 3 K += Y+ Y+^T (K range [0, dyn[1])), 4 K -= Y- Y-^T
+    // (K range [dyn[1], dyn[1] + dyn[2]))
+    const int *dyn;
+    int dyn_mode;
 };
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_ST = 4, TC_KCH = KFLUSH / TC_BK;
@@ -197,10 +208,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         nj = mi + t;
     }
+    // form selected on the device: a CTA with no work returns before it
+    // touches barriers or tensor memory (the test is uniform over the CTA)
+    int koff = g.koff, klen = g.klen;
+    if (g.dyn_mode) {
+        const int low = g.dyn[0], rp = g.dyn[1], rn = g.dyn[2];
+        if (g.dyn_mode == 1 && low) return;
+        if (g.dyn_mode == 2 && (!low || nj * TC_BN >= rp + rn)) return;
+        if (g.dyn_mode == 3) {
+            if (!low || rp == 0) return;
+            koff = 0;
+            klen = rp;
+        }
+        if (g.dyn_mode == 4) {
+            if (!low || rn == 0) return;
+            koff = rp;
+            klen = rn;
+        }
+    }
     const int per = (g.nb + g.bsplit - 1) / g.bsplit;
     const int b0 = blockIdx.z * per, b1 = min(g.nb, b0 + per);
     const int row0 = mi * TC_BM, col0 = nj * TC_BN;
-    const int nk = g.klen / TC_BK, nkc = (nk + TC_KCH - 1) / TC_KCH;
+    const int nk = klen / TC_BK, nkc = (nk + TC_KCH - 1) / TC_KCH;
 
     if (tid == TC_PROD) {
         for (int i = 0; i < TC_ST; ++i) {
@@ -233,10 +262,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int c = 0;                // accumulator chunks completed
             auto issue = [&](const TcCursor &q, int slot) {
                 uint8_t *a = tiles_gen + (size_t)slot * 2 * TC_TILE_BYTES;
-                const int x = g.koff + q.kb * TC_BK;
+                const int x = koff + q.kb * TC_BK;
                 tc::mbar_expect_tx(&full[slot], 2 * TC_TILE_BYTES);
-                tc::tma_load_2d(a, &tmA, &full[slot], x, q.b * g.a_batch_rows + q.s * g.a_slice_rows + row0);
-                tc::tma_load_2d(a + TC_TILE_BYTES, &tmB, &full[slot], x, q.b * g.b_batch_rows + q.t * g.b_slice_rows + col0);
+                tc::tma_load_2d(a, &tmA, &full[slot], x, g.a_row0 + q.b * g.a_batch_rows + q.s * g.a_slice_rows + row0);
+                tc::tma_load_2d(a + TC_TILE_BYTES, &tmB, &full[slot], x, g.b_row0 + q.b * g.b_batch_rows + q.t * g.b_slice_rows + col0);
             };
             for (; j < TC_ST - 1 && !lc.done; ++j) {
                 issue(lc, (int)(j % TC_ST));
@@ -409,8 +438,15 @@ __global__ void k_kpart_reduce(int n, int ldp, int splits, long long pstride, co
 // exactly from the two significands as a signed 64-bit integer (bits of lo
 // below 2^0 are dropped).
 __global__ void k_ozaki_slice_pair(const float2 *__restrict__ X, int rows, int cols, int ld, long long bstride, int rows_pad,
-                                   int cols_pad, int S, int B, __nv_bfloat16 *__restrict__ out, int *__restrict__ ex)
+                                   int cols_pad, int S, int B, __nv_bfloat16 *__restrict__ out, int *__restrict__ ex,
+                                   const int *__restrict__ dyn, int dyn_mode)
 {
+    // dyn_mode 1: dense form only; 2: low-rank Y, whose first dyn[1] + dyn[2] columns are live
+    if (dyn_mode == 1 && dyn[0]) return;
+    if (dyn_mode == 2) {
+        if (!dyn[0]) return;
+        cols = min(cols, dyn[1] + dyn[2]);
+    }
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= (long long)B * rows_pad) return;
@@ -449,22 +485,6 @@ __global__ void k_ozaki_slice_pair(const float2 *__restrict__ X, int rows, int c
     }
 }
 
-// C^T of the low-rank factor: row k' of Ct is eigenvector idx[k'] times
-// sqrt|lambda|; rows beyond r are zero.  V column-major (column = vector).
-__global__ void k_lowrank_factor(int n, const double *__restrict__ V, const double *__restrict__ W, const int *__restrict__ idx, int r,
-                                 int rpad, double *__restrict__ Ct)
-{
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)rpad * n) return;
-    const int kr = (int)(e / n), i = (int)(e % n);
-    double v = 0.0;
-    if (kr < r) {
-        const int j = idx[kr];
-        v = V[(size_t)j * n + i] * sqrt(fabs(W[j]));
-    }
-    Ct[e] = v;
-}
-
 static unsigned blocks_for_rows(long long rows) { return (unsigned)((rows * 32 + 255) / 256); }
 
 static void slice(const double *X, int rows, int cols, int ld, long long bstride, int rows_pad, int cols_pad, int S, int B,
@@ -474,10 +494,10 @@ static void slice(const double *X, int rows, int cols, int ld, long long bstride
 }
 
 static void slice_pair(const float2 *X, int rows, int cols, int ld, long long bstride, int rows_pad, int cols_pad, int S, int B,
-                       __nv_bfloat16 *out, int *ex, cudaStream_t st)
+                       __nv_bfloat16 *out, int *ex, const int *dyn, int dyn_mode, cudaStream_t st)
 {
     k_ozaki_slice_pair<<<blocks_for_rows((long long)B * rows_pad), 256, 0, st>>>(X, rows, cols, ld, bstride, rows_pad, cols_pad, S, B, out,
-                                                                                  ex);
+                                                                                  ex, dyn, dyn_mode);
 }
 
 // batches per CTA of a tcgen05 GEMM launch: about two waves of CTAs
@@ -524,7 +544,9 @@ static bool slice_map(CUtensorMap *m, const __nv_bfloat16 *base, long long rows,
 }
 
 // Called once per plan after the mixed workspace exists: tensor maps of the
-// fixed slice buffers, the exchange partial sums, the kernels' shared memory.
+// fixed slice buffers (the low-rank Y slices use a fixed K extent of rcap
+// columns, of which a build uses its rank's share), the exchange partial
+// sums, the kernels' shared memory.
 int ozaki_setup_tc(Plan *P)
 {
     Workspace &w = P->ws;
@@ -532,7 +554,8 @@ int ozaki_setup_tc(Plan *P)
     const int npad = w.npad, n = P->nbf, S = w.oz_slices;
     const long long big_rows = 2LL * w.gc * S * npad;
     if (!slice_map(&w.tm_Ms, w.Ms, big_rows, npad) || !slice_map(&w.tm_Zd, w.Zs, big_rows, npad) ||
-        !slice_map(&w.tm_Ds, w.Ds, (long long)S * npad, npad) || !slice_map(&w.tm_Cs, w.Cs, (long long)S * npad, npad))
+        !slice_map(&w.tm_Ds, w.Ds, (long long)S * npad, npad) || !slice_map(&w.tm_Cs, w.Cs, (long long)S * npad, npad) ||
+        (w.lr.rcap > 0 && !slice_map(&w.tm_Zl, w.Zs, big_rows, w.lr.rcap)))
         return fail(JK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the exchange slice buffers");
     const int nt = npad / TC_BM, ntri = nt * (nt + 1) / 2;
     w.kpart_splits = std::max(1, std::min(32, (4 * 152 + ntri / 2) / ntri));
@@ -562,141 +585,190 @@ int ozaki_finish(Plan *P, cudaStream_t st)
     return check("exchange partial-sum reduction");
 }
 
-// Start of a build (mixed precision): slices of D' for the dense form and,
-// when the plan has a solver, the eigendecomposition of D' whose eigenvalues
-// are copied to pinned host memory (read back later by ozaki_prepare_lowrank,
-// after the real-space kernels, so the copy never stalls the stream).
+// Start of a build (mixed precision): slices of D' for the dense form, the
+// pivoted LDL^T of D' on the device (rank and form in w.lr.dyn) and the
+// slices of its packed factor rows.  Nothing here waits for the device.
 int ozaki_begin(Plan *P, cudaStream_t st)
 {
     Workspace &w = P->ws;
     const int n = P->nbf;
+    w.chunk_log.clear();
     slice(w.Dp, n, n, n, 0, w.npad, w.npad, w.oz_slices, 1, w.Ds, w.Dex, st);
     cudaMemsetAsync(w.Kpart, 0, (size_t)w.kpart_splits * n * n * sizeof(double), st);
-    w.lowrank = false;
-    if (!w.solver) return check("density slices");
-    if (cusolverDnSetStream(w.solver, st) != CUSOLVER_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cusolverDnSetStream failed");
-    cudaMemcpyAsync(w.eigV, w.Dp, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st);
-    if (cusolverDnDsyevd(w.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, w.eigV, n, w.eigW, w.eigWork, w.eigLwork,
-                         w.eigInfo) != CUSOLVER_STATUS_SUCCESS)
-        return fail(JK_ERR_CUDA, "cusolverDnDsyevd failed");
-    cudaMemcpyAsync(w.eigW_host, w.eigW, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(w.eig_done, st);
-    return check("eigendecomposition of D");
-}
-
-// After the real-space phase: decide between the dense and the low-rank form
-// from the eigenvalues and, for low rank, form C^T and its slices.
-int ozaki_prepare_lowrank(Plan *P, cudaStream_t st)
-{
-    Workspace &w = P->ws;
-    w.lowrank = false;
-    if (!w.solver) return JK_OK;
-    if (cudaEventSynchronize(w.eig_done) != cudaSuccess) return fail(JK_ERR_CUDA, "eigendecomposition failed");
-    const int n = P->nbf;
-    double wmax = 0;
-    for (int i = 0; i < n; ++i) wmax = std::max(wmax, std::fabs(w.eigW_host[i]));
-    std::vector<int> pos, neg;
-    for (int i = n - 1; i >= 0; --i)
-        if (w.eigW_host[i] > 1e-10 * wmax) pos.push_back(i);
-    for (int i = 0; i < n; ++i)
-        if (w.eigW_host[i] < -1e-10 * wmax) neg.push_back(i);
-    const int rp = ((int)pos.size() + 127) / 128 * 128, rn = ((int)neg.size() + 127) / 128 * 128;
-    if (wmax == 0 || rp + rn > (6 * w.npad) / 10) return JK_OK;  // not worth it: dense form
-    std::vector<int> idx(rp + rn, 0);
-    for (size_t k = 0; k < pos.size(); ++k) idx[k] = pos[k];
-    for (size_t k = 0; k < neg.size(); ++k) idx[rp + k] = neg[k];
-    cudaMemcpyAsync(w.eigIdx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, st);
-    // the two column groups share one C^T buffer: rows [0, rp) and [rp, rp + rn)
-    const long long e1 = (long long)rp * n, e2 = (long long)rn * n;
-    if (rp) k_lowrank_factor<<<(unsigned)((e1 + 255) / 256), 256, 0, st>>>(n, w.eigV, w.eigW, w.eigIdx, (int)pos.size(), rp, w.Ct);
-    if (rn)
-        k_lowrank_factor<<<(unsigned)((e2 + 255) / 256), 256, 0, st>>>(n, w.eigV, w.eigW, w.eigIdx + rp, (int)neg.size(), rn, w.Ct + e1);
-    slice(w.Ct, rp + rn, n, n, 0, rp + rn, w.npad, w.oz_slices, 1, w.Cs, w.Cex, st);
-    cudaStreamSynchronize(st);  // idx is a host vector that must outlive the copy
-    if (!slice_map(&w.tm_Zl, w.Zs, 2LL * w.gc * w.oz_slices * w.npad, rp + rn))
-        return fail(JK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the low-rank slices");
-    w.lowrank = true;
-    w.rpos = rp;
-    w.rneg = rn;
-    return check("low-rank factor");
+    int rc = lowrank_factor(w.Dp, n, w.lr.rcap, 1e-12, w.lr, w.err, st);
+    if (rc) return rc;
+    if (w.lr.rcap > 0) slice(w.lr.Ct, w.lr.rcap, n, n, 0, w.lr.rcap, w.npad, w.oz_slices, 1, w.Cs, w.Cex, st);
+    return check("density slices and low-rank factor");
 }
 
 // K_LR += sum_b M_b D M_b for the m2 slabs of one G chunk, with S slices
 // per operand (the density or low-rank factor slices, cut once with
 // oz_slices, are used through their first S slices: a balanced-digit
-// expansion truncated after S digits).
-int ozaki_exchange_chunk(Plan *P, int m2, int S, cudaStream_t st)
+// expansion truncated after S digits).  Both forms are enqueued; the
+// kernels of the form the factorisation did not choose return at once.
+int ozaki_exchange_chunk(Plan *P, int chunk, const double *Mc, int m2, int S, cudaStream_t st)
 {
     Workspace &w = P->ws;
     const int n = P->nbf, npad = w.npad;
     if (S < 1 || S > w.oz_slices) return fail(JK_ERR_INVALID, "slice count outside 1..oz_slices");
     const int nt = npad / TC_BM, ntri = nt * (nt + 1) / 2;
     PhaseTimer &tm = P->timer;
-    const double prods = S * (S + 1) / 2.0;
+    w.chunk_log.push_back({m2, S});
+    const int *dyn = w.lr.dyn;
+    // the slab's slices: in the chunk buffer, or in the reciprocal cache
+    // (cut once, by the build that fills it)
+    RecipCache &cc = P->cache;
+    const bool cached = cc.on && cc.Ms;
+    __nv_bfloat16 *Ms = cached ? cc.Ms + (size_t)cc.row0[chunk] * npad : w.Ms;
+    int *Mex = cached ? cc.Mex + cc.ex0[chunk] : w.Mex;
+    const CUtensorMap &tmM = cached ? cc.tm_Ms : w.tm_Ms;
+    const int mrow0 = cached ? (int)cc.row0[chunk] : 0;
     int ev = tm.start(8);
-    slice(w.M, n, n, n, (long long)n * n, npad, npad, S, m2, w.Ms, w.Mex, st);
+    if (!cached || !cc.valid) slice(Mc, n, n, n, (long long)n * n, npad, npad, S, m2, Ms, Mex, st);
     tm.stop(8, ev, 1);
-    if (!w.lowrank) {
-        // Zt_b = (D M_b)^T, as (hi, lo) pairs
+    {
+        // dense form: Zt_b = (D M_b)^T, as (hi, lo) pairs ...
         TcArgs t{};
         t.a_batch_rows = 0; t.a_slice_rows = npad; t.b_batch_rows = S * npad; t.b_slice_rows = npad;
-        t.Aex = w.Dex; t.a_exb = 0; t.Bex = w.Mex; t.b_exb = npad;
+        t.Aex = w.Dex; t.a_exb = 0; t.Bex = Mex; t.b_exb = npad; t.b_row0 = mrow0;
         t.koff = 0; t.klen = npad; t.S = S; t.nb = m2; t.ntm = nt; t.ntn = nt;
         t.out = reinterpret_cast<float2 *>(w.Z); t.out_rows = n; t.out_cols = n; t.o_bstride = (long long)n * n; t.ldo = n;
         t.transpose = 1; t.err = w.err; t.bsplit = tc_splits(nt * nt, m2);
+        t.dyn = dyn; t.dyn_mode = 1;
         ev = tm.start(7);
-        launch_tc(0, w.tm_Ds, w.tm_Ms, t, dim3(nt * nt, 1, t.bsplit), st);
+        launch_tc(0, w.tm_Ds, tmM, t, dim3(nt * nt, 1, t.bsplit), st);
         tm.stop(7, ev, 1);
-        w.mma_flops += prods * 2.0 * npad * (double)npad * npad * m2;
         ev = tm.start(8);
-        slice_pair(reinterpret_cast<const float2 *>(w.Z), n, n, n, (long long)n * n, npad, npad, S, m2, w.Zs, w.Zex, st);
+        slice_pair(reinterpret_cast<const float2 *>(w.Z), n, n, n, (long long)n * n, npad, npad, S, m2, w.Zs, w.Zex, dyn, 1, st);
         tm.stop(8, ev, 1);
-        // K += sum_b M_b Z_b, upper tiles into the float-pair partials
+        // ... then K += sum_b M_b Z_b, upper tiles into the float-pair partials
         TcArgs k{};
         k.a_batch_rows = S * npad; k.a_slice_rows = npad; k.b_batch_rows = S * npad; k.b_slice_rows = npad;
-        k.Aex = w.Mex; k.a_exb = npad; k.Bex = w.Zex; k.b_exb = npad;
+        k.Aex = Mex; k.a_exb = npad; k.Bex = w.Zex; k.b_exb = npad; k.a_row0 = mrow0;
         k.koff = 0; k.klen = npad; k.S = S; k.nb = m2; k.bsplit = std::min(w.kpart_splits, m2); k.ntm = nt; k.ntn = nt;
         k.part = w.Kpart; k.part_stride = (long long)n * n; k.ldp = n; k.out_rows = n; k.out_cols = n; k.sign = 1.f;
-        k.err = w.err;
+        k.err = w.err; k.dyn = dyn; k.dyn_mode = 1;
         ev = tm.start(7);
-        launch_tc(1, w.tm_Ms, w.tm_Zd, k, dim3(ntri, 1, k.bsplit), st);
+        launch_tc(1, tmM, w.tm_Zd, k, dim3(ntri, 1, k.bsplit), st);
         tm.stop(7, ev, 1);
-        w.mma_flops += prods * 2.0 * TC_BM * (double)TC_BN * npad * ntri * m2;
-        return check("split-precision exchange GEMM (dense)");
     }
-    const int rt = w.rpos + w.rneg;
-    // Y_b = M_b [C+ C-]  (n x rt, row-major, (hi, lo) pairs)
-    TcArgs y{};
-    y.a_batch_rows = S * npad; y.a_slice_rows = npad; y.b_batch_rows = 0; y.b_slice_rows = rt;
-    y.Aex = w.Mex; y.a_exb = npad; y.Bex = w.Cex; y.b_exb = 0;
-    y.koff = 0; y.klen = npad; y.S = S; y.nb = m2; y.ntm = nt; y.ntn = rt / TC_BN;
-    y.out = reinterpret_cast<float2 *>(w.Z); y.out_rows = n; y.out_cols = rt; y.o_bstride = (long long)n * rt; y.ldo = rt;
-    y.transpose = 0; y.err = w.err; y.bsplit = tc_splits(nt * (rt / TC_BN), m2);
-    ev = tm.start(7);
-    launch_tc(0, w.tm_Ms, w.tm_Cs, y, dim3(nt * (rt / TC_BN), 1, y.bsplit), st);
-    tm.stop(7, ev, 1);
-    w.mma_flops += prods * 2.0 * npad * (double)rt * npad * m2;
-    ev = tm.start(8);
-    slice_pair(reinterpret_cast<const float2 *>(w.Z), n, rt, rt, (long long)n * rt, npad, rt, S, m2, w.Zs, w.Zex, st);
-    tm.stop(8, ev, 1);
-    // K += sum_b Y+_b Y+_b^T - Y-_b Y-_b^T  (symmetric, K range per group)
-    for (int grp = 0; grp < 2; ++grp) {
-        const int klen = grp == 0 ? w.rpos : w.rneg;
-        if (!klen) continue;
-        TcArgs k{};
-        k.a_batch_rows = S * npad; k.a_slice_rows = npad; k.b_batch_rows = S * npad; k.b_slice_rows = npad;
-        k.Aex = w.Zex; k.a_exb = npad; k.Bex = w.Zex; k.b_exb = npad;
-        k.koff = grp == 0 ? 0 : w.rpos; k.klen = klen; k.S = S; k.nb = m2; k.bsplit = std::min(w.kpart_splits, m2); k.ntm = nt;
-        k.ntn = nt;
-        k.part = w.Kpart; k.part_stride = (long long)n * n; k.ldp = n; k.out_rows = n; k.out_cols = n;
-        k.sign = grp == 0 ? 1.f : -1.f;
-        k.err = w.err;
+    const int rcap = w.lr.rcap;
+    if (rcap > 0) {
+        // low-rank form: Y_b = M_b [C+ C-]  (n x rcap, row-major, (hi, lo) pairs; live columns up to the rank)
+        TcArgs y{};
+        y.a_batch_rows = S * npad; y.a_slice_rows = npad; y.b_batch_rows = 0; y.b_slice_rows = rcap;
+        y.Aex = Mex; y.a_exb = npad; y.Bex = w.Cex; y.b_exb = 0; y.a_row0 = mrow0;
+        y.koff = 0; y.klen = npad; y.S = S; y.nb = m2; y.ntm = nt; y.ntn = rcap / TC_BN;
+        y.out = reinterpret_cast<float2 *>(w.Z); y.out_rows = n; y.out_cols = rcap; y.o_bstride = (long long)n * rcap; y.ldo = rcap;
+        y.transpose = 0; y.err = w.err; y.bsplit = tc_splits(nt * (rcap / TC_BN), m2);
+        y.dyn = dyn; y.dyn_mode = 2;
         ev = tm.start(7);
-        launch_tc(1, w.tm_Zl, w.tm_Zl, k, dim3(ntri, 1, k.bsplit), st);
+        launch_tc(0, tmM, w.tm_Cs, y, dim3(nt * (rcap / TC_BN), 1, y.bsplit), st);
         tm.stop(7, ev, 1);
-        w.mma_flops += prods * 2.0 * TC_BM * (double)TC_BN * klen * ntri * m2;
+        ev = tm.start(8);
+        slice_pair(reinterpret_cast<const float2 *>(w.Z), n, rcap, rcap, (long long)n * rcap, npad, rcap, S, m2, w.Zs, w.Zex, dyn, 2, st);
+        tm.stop(8, ev, 1);
+        // K += sum_b Y+_b Y+_b^T - Y-_b Y-_b^T  (symmetric, K range per group)
+        for (int grp = 0; grp < 2; ++grp) {
+            TcArgs k{};
+            k.a_batch_rows = S * npad; k.a_slice_rows = npad; k.b_batch_rows = S * npad; k.b_slice_rows = npad;
+            k.Aex = w.Zex; k.a_exb = npad; k.Bex = w.Zex; k.b_exb = npad;
+            k.koff = 0; k.klen = 0; k.S = S; k.nb = m2; k.bsplit = std::min(w.kpart_splits, m2); k.ntm = nt;
+            k.ntn = nt;
+            k.part = w.Kpart; k.part_stride = (long long)n * n; k.ldp = n; k.out_rows = n; k.out_cols = n;
+            k.sign = grp == 0 ? 1.f : -1.f;
+            k.err = w.err; k.dyn = dyn; k.dyn_mode = grp == 0 ? 3 : 4;
+            ev = tm.start(7);
+            launch_tc(1, w.tm_Zl, w.tm_Zl, k, dim3(ntri, 1, k.bsplit), st);
+            tm.stop(7, ev, 1);
+        }
     }
-    return check("split-precision exchange GEMM (low rank)");
+    return check("split-precision exchange GEMM");
+}
+
+// Reciprocal cache: every chunk's structure-factor slab (FP64) and, for
+// mixed plans, its slices and row exponents, if the total fits max_bytes.
+// The caller holds the plan's lock and has waited for its last build.
+void release_cache(Plan *P)
+{
+    RecipCache &c = P->cache;
+    if (c.M) cudaFree(c.M);
+    if (c.Ms) cudaFree(c.Ms);
+    if (c.Mex) cudaFree(c.Mex);
+    c = RecipCache{};
+}
+
+int cache_reciprocal(Plan *P, size_t max_bytes)
+{
+    release_cache(P);
+    if (max_bytes == 0) return JK_OK;
+    Workspace &w = P->ws;
+    const int ng = (int)(P->gvec.size() / 4);
+    const size_t n2 = (size_t)P->nbf * P->nbf;
+    RecipCache &c = P->cache;
+    size_t bM = 2 * (size_t)ng * n2 * sizeof(double), bS = 0, bX = 0;
+    long long rows = 0, ex = 0;
+    const bool mixed = P->precision == JK_MIXED;
+    if (mixed) {
+        for (int g0 = 0, ch = 0; g0 < ng; g0 += w.gc, ++ch) {
+            const int m2 = 2 * std::min(w.gc, ng - g0), S = w.chunk_slices[ch];
+            c.row0.push_back(rows);
+            c.ex0.push_back(ex);
+            rows += (long long)m2 * S * w.npad;
+            ex += (long long)m2 * w.npad;
+        }
+        bS = (size_t)rows * w.npad * sizeof(__nv_bfloat16);
+        bX = (size_t)ex * sizeof(int);
+        if (rows >= (1LL << 31)) {
+            c = RecipCache{};
+            return fail(JK_ERR_OOM, "reciprocal cache: too many slice rows for one tensor map");
+        }
+    }
+    const size_t need = bM + bS + bX;
+    if (need > max_bytes) {
+        c = RecipCache{};
+        return fail(JK_ERR_OOM, "reciprocal cache needs " + std::to_string(need) + " bytes, above the limit given");
+    }
+    if (cudaMalloc((void **)&c.M, bM) != cudaSuccess || (mixed && cudaMalloc((void **)&c.Ms, bS) != cudaSuccess) ||
+        (mixed && cudaMalloc((void **)&c.Mex, bX) != cudaSuccess)) {
+        cudaGetLastError();
+        release_cache(P);
+        return fail(JK_ERR_OOM, "cudaMalloc failed for the reciprocal cache");
+    }
+    // entries of shell pairs without images are never written
+    if (cudaMemset(c.M, 0, bM) != cudaSuccess) {
+        release_cache(P);
+        return fail(JK_ERR_CUDA, "cudaMemset failed for the reciprocal cache");
+    }
+    if (mixed && !slice_map(&c.tm_Ms, c.Ms, rows, w.npad)) {
+        release_cache(P);
+        return fail(JK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the reciprocal cache");
+    }
+    c.on = true;
+    c.valid = false;
+    c.bytes = need;
+    return JK_OK;
+}
+
+// BF16 MMA flops the exchange GEMMs of the last build issued, from its chunk
+// log and the form and rank the device chose (dyn read back after the build).
+double ozaki_mma_flops(const Plan *P, const int dyn[3])
+{
+    const Workspace &w = P->ws;
+    const int npad = w.npad, nt = npad / TC_BM, ntri = nt * (nt + 1) / 2;
+    double f = 0;
+    for (auto &c : w.chunk_log) {
+        const int m2 = c.first, S = c.second;
+        const double prods = S * (S + 1) / 2.0;
+        if (!dyn[0]) {
+            f += prods * 2.0 * npad * (double)npad * npad * m2;
+            f += prods * 2.0 * TC_BM * (double)TC_BN * npad * ntri * m2;
+        } else {
+            f += prods * 2.0 * npad * (double)(dyn[1] + dyn[2]) * npad * m2;
+            f += prods * 2.0 * TC_BM * (double)TC_BN * (dyn[1] + dyn[2]) * ntri * m2;
+        }
+    }
+    return f;
 }
 
 }  // namespace jk

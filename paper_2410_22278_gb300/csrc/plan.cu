@@ -153,6 +153,101 @@ static void herm_E_host(int la, int lb, double PA, double PB, double oo2p, doubl
         }
 }
 
+// Boys function F_m(T), m = 0..mmax, on the host: F_mmax by its convergent
+// series e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) and downward
+// recursion below T = 40; above, F_0 = (1/2) sqrt(pi/T) erf(sqrt T) and
+// upward recursion (stable for T > mmax).
+static void boys_host(int mmax, double T, double *F)
+{
+    const double e = std::exp(-T);
+    if (T < 40.0) {
+        double term = 1.0 / (2 * mmax + 1), sum = term;
+        for (int k = 1; k < 600 && term > 1e-18 * sum; ++k) {
+            term *= 2.0 * T / (2 * mmax + 2 * k + 1);
+            sum += term;
+        }
+        F[mmax] = e * sum;
+        for (int m = mmax - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) / (2 * m + 1);
+    } else {
+        F[0] = 0.5 * std::sqrt(kPi / T) * std::erf(std::sqrt(T));
+        for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) / (2.0 * T);
+    }
+}
+
+// Exact Schwarz factor of one shell-pair image: sqrt of the largest diagonal
+// free-space Coulomb integral (ab|ab) over its Cartesian components (with
+// their normalisation factors f_a f_b), summed over the image's primitive
+// pairs by McMurchie-Davidson (Eqs. E_recursion_*, R_recursion).  Every
+// term of the lattice-summed real-space ERI is a free-space integral of a
+// translated pair, so |(ab|cd(R))| <= Q_ab Q_cd bounds it term by term.
+static double exact_schwarz(int la, int lb, const std::vector<PpiRec> &pv, const double *fa, const double *fb)
+{
+    const int L = 2 * (la + lb), D = L + 1;
+    const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+    const int npp = (int)pv.size();
+    std::vector<double> E((size_t)npp * 3 * 45);  // [pair][axis][i][j][t]
+    for (int i = 0; i < npp; ++i)
+        for (int ax = 0; ax < 3; ++ax) {
+            double e[3][3][5];
+            herm_E_host(la, lb, pv[i].PA[ax], pv[i].PB[ax], 0.5 / pv[i].p, e);
+            std::memcpy(&E[((size_t)i * 3 + ax) * 45], e, sizeof e);
+        }
+    auto Eat = [&](int i, int ax, int a, int b, int t) { return E[((size_t)i * 3 + ax) * 45 + (a * 3 + b) * 5 + t]; };
+    std::vector<double> diag((size_t)na * nb, 0.0);
+    std::vector<double> R((size_t)D * D * D * D), F(D);
+    auto Ridx = [&](int n, int t, int u, int v) -> double & { return R[(((size_t)n * D + t) * D + u) * D + v]; };
+    for (int i = 0; i < npp; ++i)
+        for (int j = 0; j < npp; ++j) {
+            const double p = pv[i].p, q = pv[j].p, alpha = p * q / (p + q);
+            const double X[3] = {pv[i].P[0] - pv[j].P[0], pv[i].P[1] - pv[j].P[1], pv[i].P[2] - pv[j].P[2]};
+            boys_host(L, alpha * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]), F.data());
+            // R^n_{tuv} for t+u+v <= L - n
+            double f = 1.0;
+            for (int n = 0; n <= L; ++n) {
+                Ridx(n, 0, 0, 0) = f * F[n];
+                f *= -2.0 * alpha;
+            }
+            for (int n = L - 1; n >= 0; --n)
+                for (int s = 1; s <= L - n; ++s)
+                    for (int t = 0; t <= s; ++t)
+                        for (int u = 0; u <= s - t; ++u) {
+                            const int v = s - t - u;
+                            double r;
+                            if (t > 0) r = X[0] * Ridx(n + 1, t - 1, u, v) + (t > 1 ? (t - 1) * Ridx(n + 1, t - 2, u, v) : 0.0);
+                            else if (u > 0) r = X[1] * Ridx(n + 1, t, u - 1, v) + (u > 1 ? (u - 1) * Ridx(n + 1, t, u - 2, v) : 0.0);
+                            else r = X[2] * Ridx(n + 1, t, u, v - 1) + (v > 1 ? (v - 1) * Ridx(n + 1, t, u, v - 2) : 0.0);
+                            Ridx(n, t, u, v) = r;
+                        }
+            const double pref = 2.0 * std::pow(kPi, 2.5) / (p * q * std::sqrt(p + q)) * pv[i].K * pv[j].K;
+            for (int a = 0; a < na; ++a)
+                for (int b = 0; b < nb; ++b) {
+                    int ea[3], eb[3];
+                    cart_exps(la, a, ea);
+                    cart_exps(lb, b, eb);
+                    double v = 0;
+                    for (int t0 = 0; t0 <= ea[0] + eb[0]; ++t0)
+                        for (int t1 = 0; t1 <= ea[1] + eb[1]; ++t1)
+                            for (int t2 = 0; t2 <= ea[2] + eb[2]; ++t2) {
+                                const double et = Eat(i, 0, ea[0], eb[0], t0) * Eat(i, 1, ea[1], eb[1], t1) * Eat(i, 2, ea[2], eb[2], t2);
+                                if (et == 0.0) continue;
+                                for (int s0 = 0; s0 <= ea[0] + eb[0]; ++s0)
+                                    for (int s1 = 0; s1 <= ea[1] + eb[1]; ++s1)
+                                        for (int s2 = 0; s2 <= ea[2] + eb[2]; ++s2) {
+                                            const double es = Eat(j, 0, ea[0], eb[0], s0) * Eat(j, 1, ea[1], eb[1], s1) *
+                                                              Eat(j, 2, ea[2], eb[2], s2);
+                                            const double sg = ((s0 + s1 + s2) & 1) ? -1.0 : 1.0;
+                                            v += et * es * sg * Ridx(0, t0 + s0, t1 + s1, t2 + s2);
+                                        }
+                            }
+                    diag[(size_t)a * nb + b] += pref * v;
+                }
+        }
+    double m = 0;
+    for (int a = 0; a < na; ++a)
+        for (int b = 0; b < nb; ++b) m = std::max(m, std::fabs(diag[(size_t)a * nb + b]) * fa[a] * fa[a] * fb[b] * fb[b]);
+    return std::sqrt(m);
+}
+
 // F_m(T_k) table by the convergent series at the top order and downward
 // recursion, in long double.
 void boys_table(int ncol, int npts, double inv_step, std::vector<double> &out)
@@ -238,6 +333,9 @@ PlanDev Plan::dev() const
     // sums many such terms, so the sphere is drawn at delta_Ewald-R / 10
     // (plus an angular-momentum margin in the kernels).
     d.log_ewald_R = (float)std::log(cut.ewald_R * 1e-1);
+    // B_i B_j below this means 2 pi^{5/2} |K_i K_j| / (pq sqrt(p+q)) < delta/10
+    d.ppB = d_ppB;
+    d.mag_thr = (float)(cut.ewald_R * 1e-1 / (24.739424126 * 1.001));
     d.volume = volume;
     for (int a = 0; a < 3; ++a)
         d.hplane[a] = (float)(1.0 / std::sqrt(Finv[3 * a] * Finv[3 * a] + Finv[3 * a + 1] * Finv[3 * a + 1] + Finv[3 * a + 2] * Finv[3 * a + 2]));
@@ -309,10 +407,15 @@ static int alloc_ws(Plan *P)
         return true;
     };
     bool ok = al(&w.gtab, std::max<size_t>(1, P->pvals.size()) * (size_t)gc) && al(&w.Dp, n2) && al(&w.X, n2) && al(&w.Y, n2) && al(&w.JLR, n2) && al(&w.KLR, n2) && al(&w.T1, n2) &&
-              al(&w.T2, n2) && al(&w.M, 2 * (size_t)gc * n2) && al(&w.Z, 2 * (size_t)gc * n2) && al(&w.rho, 2 * (size_t)gc) &&
+              al(&w.T2, n2) && al(&w.M, 2 * (size_t)gc * n2) && al(&w.Z, 2 * (size_t)gc * n2) && al(&w.rho, 2 * (size_t)gc) && al(&w.rho_part, 2 * (size_t)gc * kSlabSplitsMax) &&
               al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16) && (!mixed || al((double **)&w.Dpf, (n2 + 1) / 2)) &&
               (!mixed || al((double **)&w.dmaxf, ((size_t)P->nshell * P->nshell + 1) / 2));
     if (!ok) return fail(JK_ERR_OOM, "cudaMalloc failed for build workspace");
+    // the structure-factor kernels write only the entries of shell pairs with
+    // images, the same ones for every G; the others must read as zero
+    if (cudaMemset(w.M, 0, 2 * (size_t)gc * n2 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(w.Z, 0, 2 * (size_t)gc * n2 * sizeof(double)) != cudaSuccess)
+        return fail(JK_ERR_CUDA, "cudaMemset failed for the structure-factor slab");
     if (mixed) {
         const size_t sl = (size_t)w.oz_slices * w.npad * w.npad;
         auto alb = [&](__nv_bfloat16 **ptr, size_t count) -> bool {
@@ -330,20 +433,20 @@ static int alloc_ws(Plan *P)
         bytes += std::max<size_t>(1, P->pvals.size()) * (size_t)gc * sizeof(float2);
         if (!alb(&w.Ms, 2 * (size_t)gc * sl) || !alb(&w.Zs, 2 * (size_t)gc * sl) || !alb(&w.Ds, sl) || !alb(&w.Cs, sl) ||
             !ali(&w.Mex, 2 * (size_t)gc * w.npad) || !ali(&w.Zex, 2 * (size_t)gc * w.npad) || !ali(&w.Dex, w.npad) ||
-            !ali(&w.Cex, w.npad) || !ali(&w.eigIdx, w.npad) || !ali(&w.eigInfo, 1) || !al(&w.eigV, n2) || !al(&w.eigW, P->nbf) ||
-            !al(&w.Ct, (size_t)w.npad * P->nbf))
+            !ali(&w.Cex, w.npad))
             return fail(JK_ERR_OOM, "cudaMalloc failed for tensor-core exchange workspace");
-        // eigensolver for the low-rank form of D (closed-shell densities have rank n_occ)
-        if (cusolverDnCreate(&w.solver) != CUSOLVER_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cusolverDnCreate failed");
-        if (cusolverDnDsyevd_bufferSize(w.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, P->nbf, w.eigV, P->nbf, w.eigW,
-                                        &w.eigLwork) != CUSOLVER_STATUS_SUCCESS)
-            return fail(JK_ERR_CUDA, "cusolverDnDsyevd_bufferSize failed");
-        if (!al(&w.eigWork, (size_t)std::max(1, w.eigLwork))) return fail(JK_ERR_OOM, "cudaMalloc failed for eigensolver");
-        if (cudaMallocHost((void **)&w.eigW_host, sizeof(double) * P->nbf) != cudaSuccess) return fail(JK_ERR_OOM, "pinned buffer");
-        if (cudaEventCreateWithFlags(&w.eig_done, cudaEventDisableTiming) != cudaSuccess) return fail(JK_ERR_CUDA, "event");
+        // low-rank form of D: worth it while the padded rank stays within 60%
+        // of npad (closed-shell densities have rank n_occ)
+        LowRankWs &lr = w.lr;
+        lr.rcap = (6 * w.npad / 10) / 128 * 128;
+        const size_t rc = (size_t)std::max(lr.rcap, 1);
+        if (!al(&lr.Vt, (size_t)P->nbf * rc) || !al(&lr.diag, P->nbf) || !ali(&lr.done_row, P->nbf) || !al(&lr.sgn, rc) ||
+            !ali(&lr.rowmap, rc) || !ali(&lr.dyn, 8) || !ali((int **)&lr.bar, 1) || !al(&lr.Ct, rc * P->nbf))
+            return fail(JK_ERR_OOM, "cudaMalloc failed for the low-rank factorisation");
+        cudaMemset(lr.dyn, 0, 8 * sizeof(int));
     }
     if (cudaMalloc((void **)&w.err, sizeof(unsigned)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
-    if (cudaMalloc((void **)&w.cnt, 8 * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
+    if (cudaMalloc((void **)&w.cnt, kCounters * sizeof(unsigned long long)) != cudaSuccess) return fail(JK_ERR_OOM, "cudaMalloc failed");
     if (P->precision == JK_MIXED) {
         // the FP64 share is a small fraction; the list holds up to 2% of all image quartets (at most 64 Mi entries)
         const long long want = std::min<long long>(std::max<long long>(P->n_quartets / 50, 1 << 20), 64ll << 20);
@@ -353,7 +456,7 @@ static int alloc_ws(Plan *P)
         bytes += sizeof(int2) * w.cap + 2 * sizeof(unsigned);
     }
     cudaMemset(w.err, 0, sizeof(unsigned));
-    w.bytes = bytes + sizeof(unsigned) + 8 * sizeof(unsigned long long);
+    w.bytes = bytes + sizeof(unsigned) + kCounters * sizeof(unsigned long long);
     if (P->precision == JK_MIXED) return ozaki_setup_tc(P);
     return JK_OK;
 }
@@ -381,7 +484,11 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     }
     Plan *P = new Plan();
     for (int i = 0; i < JK_NCLASS_MAX; ++i)
-        for (int j = 0; j < JK_NCLASS_MAX; ++j) P->kchunk[i][j] = 32;
+        for (int j = 0; j < JK_NCLASS_MAX; ++j) {
+            // untuned: the warp kernels for s and p class pairs, 512 kets per warp
+            P->kvariant[i][j] = (i <= 2 && j <= 2) ? 1 : 0;
+            P->kchunk[i][j] = (i <= 2 && j <= 2) ? 512 : 32;
+        }
     P->device = device;
     P->precision = precision;
     memcpy(P->L, cell->lattice, sizeof P->L);
@@ -449,6 +556,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     std::vector<SpiRec> spis;
     std::vector<std::vector<PpiRec>> spi_ppis;
     std::vector<std::vector<double2>> spi_ab;  // exponents (a, b) of each primitive pair, same order
+    std::vector<double> spi_qx;                // exact Schwarz factor of each image (exact_schwarz)
     const double *L = P->L;
     for (int I = 0; I < nshell; ++I) {
         const ShellRec &sI = P->shells[I];
@@ -522,7 +630,11 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                 {
                     std::vector<int> ord(pv.size());
                     std::iota(ord.begin(), ord.end(), 0);
-                    std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return std::fabs(pv[u].K) > std::fabs(pv[v].K); });
+                    // descending B = |K| p^{-5/4}, the separable bound of the
+                    // primitive prefactors: loops over primitives stop at the
+                    // first pair below the magnitude threshold
+                    auto Bof = [&](int u) { return std::fabs(pv[u].K) * std::pow(pv[u].p, -1.25); };
+                    std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return Bof(u) > Bof(v); });
                     std::vector<PpiRec> pv2;
                     std::vector<double2> ab2;
                     for (int o : ord) {
@@ -541,6 +653,12 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                 sr.n[2] = n[2];
                 sr.w = (I == J && n[0] == 0 && n[1] == 0 && n[2] == 0) ? 0.5f : 1.0f;
                 sr.Q = Q;
+                {
+                    double fa[6], fb[6];
+                    for (int k = 0; k < (sF.l + 1) * (sF.l + 2) / 2; ++k) fa[k] = P->compf[sF.ao + k];
+                    for (int k = 0; k < (sS.l + 1) * (sS.l + 2) / 2; ++k) fb[k] = P->compf[sS.ao + k];
+                    spi_qx.push_back(exact_schwarz(sF.l, sS.l, pv, fa, fb));
+                }
                 for (int k = 0; k < 3; ++k) sr.Pc[k] = (float)pv[0].P[k];
                 sr.ext = 0.f;
                 double Ssum = 0, pmin = 1e300;
@@ -635,23 +753,25 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
         }
         for (int i = 0; i < JK_NCLASS_MAX; ++i) P->spair_class_off[i + 1] += P->spair_class_off[i];
     }
-    // ---- quartet counts (unique pairs of images), Schwarz-significant ones
+    // ---- quartet counts (unique pairs of images): Schwarz-significant ones
+    // by the exact factors (the quartets/s unit), and the FP64 share the
+    // mixed policy would take by the Eq. 445 estimates
     {
         long long N = (long long)P->spi.size();
         P->n_quartets = N * (N + 1) / 2;
+        auto count_pairs = [N](std::vector<double> q, double thr) {
+            std::sort(q.begin(), q.end(), std::greater<double>());
+            long long cnt = 0, j = N - 1;
+            for (long long i = 0; i < N; ++i) {
+                while (j >= i && q[i] * q[j] < thr) --j;
+                if (j >= i) cnt += j - i + 1;
+            }
+            return cnt;
+        };
         std::vector<double> q(N);
         for (long long i = 0; i < N; ++i) q[i] = P->spi[i].Q;
-        std::sort(q.begin(), q.end(), std::greater<double>());
-        long long cnt = 0, cnt64 = 0;
-        long long j = N - 1, j64 = N - 1;
-        for (long long i = 0; i < N; ++i) {
-            while (j >= i && q[i] * q[j] < c.pair_cs) --j;
-            if (j >= i) cnt += j - i + 1;
-            while (j64 >= i && q[i] * q[j64] < P->mixed_tau) --j64;
-            if (j64 >= i) cnt64 += j64 - i + 1;
-        }
-        P->n_quartets_schwarz = cnt;
-        P->n_quartets_fp64 = precision == JK_FP64 ? P->n_quartets : cnt64;
+        P->n_quartets_schwarz = count_pairs(spi_qx, c.pair_cs);
+        P->n_quartets_fp64 = precision == JK_FP64 ? P->n_quartets : count_pairs(q, P->mixed_tau);
     }
     // ---- R1 candidates for the real-space sums (Section 3.3)
     {
@@ -838,8 +958,13 @@ int finish_plan_device(Plan *P)
             pf[i].K = (float)x.K;
             pf[i].pad = (float)(1.0 / x.p);
         }
+        // B = |K| p^{-5/4} per primitive pair, rounded up so that the float
+        // bound stays a bound
+        std::vector<float> pB(P->ppi.size());
+        for (size_t i = 0; i < P->ppi.size(); ++i)
+            pB[i] = (float)(std::fabs(P->ppi[i].K) * std::pow(P->ppi[i].p, -1.25) * (1.0 + 1e-6));
         std::vector<float> r1f(P->r1.begin(), P->r1.end());
-        if ((rc = upload(pf, &P->d_ppf, b)) || (rc = upload(r1f, &P->d_r1f, b))) return rc;
+        if ((rc = upload(pf, &P->d_ppf, b)) || (rc = upload(r1f, &P->d_r1f, b)) || (rc = upload(pB, &P->d_ppB, b))) return rc;
     }
     std::vector<double> tab;
     boys_table(JK_BOYS_MCOL, JK_BOYS_NPTS, JK_BOYS_INV_STEP, tab);
@@ -929,7 +1054,6 @@ int finish_plan_device(Plan *P)
     std::vector<double> zeros((size_t)P->nbf * P->nbf, 0.0);
     if ((rc = upload(zeros, &P->d_S, b))) return rc;
     if ((rc = alloc_ws(P))) return rc;
-    if (cublasCreate(&P->blas) != CUBLAS_STATUS_SUCCESS) return fail(JK_ERR_CUDA, "cublasCreate failed");
     if ((rc = compute_overlap_raw(P, 0))) return rc;
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(JK_ERR_CUDA, "plan setup kernels failed");
     return JK_OK;
@@ -939,17 +1063,14 @@ void destroy_plan(Plan *P)
 {
     if (!P) return;
     cudaSetDevice(P->device);
-    void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
+    release_cache(P);
+    void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_ppB, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
                     P->d_g0, P->d_compf, P->d_ppi_ab, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->d_ppdf, P->d_gdf, P->d_phasef, P->ws.gtab, P->ws.gtab2, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
-                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
+                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.rho_part, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
                     P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
-                    P->ws.eigV, P->ws.eigW, P->ws.eigWork, P->ws.Ct, P->ws.eigInfo, P->ws.eigIdx};
+                    P->ws.lr.Vt, P->ws.lr.diag, P->ws.lr.done_row, P->ws.lr.sgn, P->ws.lr.rowmap, P->ws.lr.dyn, P->ws.lr.bar, P->ws.lr.Ct};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    if (P->blas) cublasDestroy(P->blas);
-    if (P->ws.solver) cusolverDnDestroy(P->ws.solver);
-    if (P->ws.eigW_host) cudaFreeHost(P->ws.eigW_host);
-    if (P->ws.eig_done) cudaEventDestroy(P->ws.eig_done);
     P->timer.destroy();
     delete P;
 }

@@ -1,7 +1,5 @@
 // Host-side plan: built once per geometry (Section 3.1), then immutable.
 #pragma once
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 #include <cmath>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -12,6 +10,7 @@
 #include <vector>
 
 #include "../../include/jk.h"
+#include "dense.h"
 #include "jk_internal.h"
 
 namespace jk {
@@ -24,6 +23,12 @@ struct ClassRange {
     int b0, b1;  // spi index range
 };
 
+// Device counters of a build: per precision (base 0 FP64, 1 FP32) image
+// quartets [base], algorithmic flops [4 + base], screening and bookkeeping
+// flops [8 + base], lane-terms [12 + base] and lane slots [14 + base] of the
+// primitive loops.
+constexpr int kCounters = 16;
+
 struct Workspace {
     double *Dp = nullptr;     // D scaled by component factors
     double *X = nullptr;      // real-space J accumulator
@@ -35,12 +40,13 @@ struct Workspace {
     double *M = nullptr;      // structure-factor chunk [2*gc][n][n]
     double *Z = nullptr;      // D * M chunk, stacked
     double *rho = nullptr;    // [2*gc] density structure factors
+    double *rho_part = nullptr;  // [2*gc][kSlabSplitsMax] their partial sums
     double *dmax = nullptr;   // [nshell*nshell] max |D'| per shell block
     float *Dpf = nullptr;     // single-precision copies for the FP32 kernels (mixed precision)
     float *dmaxf = nullptr;
     double *scal = nullptr;   // small scalars (traces, energies)
     unsigned *err = nullptr;  // device check word
-    unsigned long long *cnt = nullptr;  // [0] FP64 image quartets, [1] FP32 image quartets
+    unsigned long long *cnt = nullptr;  // kCounters build counters (see above)
     int2 *big = nullptr;                // compact list of quartets sent to FP64 (mixed precision)
     unsigned *nbig = nullptr;           // [0] list length, [1] overflow count (accumulated over a build)
     unsigned cap = 0;
@@ -53,15 +59,12 @@ struct Workspace {
     std::vector<int> chunk_slices;  // slices per G chunk (mixed exchange), <= oz_slices
     __nv_bfloat16 *Ms = nullptr, *Zs = nullptr, *Ds = nullptr, *Cs = nullptr;
     int *Mex = nullptr, *Zex = nullptr, *Dex = nullptr, *Cex = nullptr;
-    // low-rank form of D (eigendecomposition on the device)
-    cusolverDnHandle_t solver = nullptr;
-    double *eigV = nullptr, *eigW = nullptr, *eigWork = nullptr, *eigW_host = nullptr, *Ct = nullptr;
-    int *eigInfo = nullptr, *eigIdx = nullptr;
-    int eigLwork = 0;
-    cudaEvent_t eig_done = nullptr;
-    bool lowrank = false;
-    int rpos = 0, rneg = 0;
-    double mma_flops = 0;  // BF16 MMA flops issued by the split-precision GEMMs of the last build
+    // low-rank form of D (pivoted LDL^T on the device, dense.cu); which form
+    // a build used is known only on the device (lr.dyn)
+    LowRankWs lr;
+    // (slabs, slices) of every exchange chunk of the last build: with the
+    // rank read back after the build they give the MMA flops it issued
+    std::vector<std::pair<int, int>> chunk_log;
     // tcgen05 form: TMA descriptors of the slice buffers (K-major rows, 128-byte
     // swizzle, 64 x 128 boxes) and per-split FP64 partial sums of the exchange
     bool tc = false;
@@ -82,6 +85,20 @@ struct PhaseTimer {
     int start(int phase);
     void stop(int phase, int ev_start, int nlaunch);
     void destroy();
+};
+
+// D-independent reciprocal data kept between builds (jk_plan_cache): the
+// structure-factor slab of every G chunk and, for mixed plans, its BF16
+// exchange slices and row exponents.  Filled by the first build after it is
+// switched on; later builds skip the structure factors and their slicing.
+struct RecipCache {
+    bool on = false, valid = false;
+    size_t bytes = 0;
+    double *M = nullptr;              // [2 * ng][n][n]
+    __nv_bfloat16 *Ms = nullptr;      // chunk c at rows [row0[c], ...) of a (rows x npad) matrix
+    int *Mex = nullptr;               // chunk c at ex0[c]
+    std::vector<long long> row0, ex0;
+    CUtensorMap tm_Ms;
 };
 
 struct Plan {
@@ -106,7 +123,8 @@ struct Plan {
     long long n_ord_shell_pairs = 0, n_ord_prim_pairs = 0, n_ord_local_pairs = 0;
     long long n_shell_pairs = 0, n_quartets = 0, n_quartets_schwarz = 0, n_quartets_fp64 = 0;
     double mixed_tau = 0;
-    int kchunk[JK_NCLASS_MAX][JK_NCLASS_MAX];  // kets per tile of the real-space kernels (autotuned)
+    int kchunk[JK_NCLASS_MAX][JK_NCLASS_MAX];    // kets per tile (or per warp) of the real-space kernels (autotuned)
+    int kvariant[JK_NCLASS_MAX][JK_NCLASS_MAX];  // kernel family: 0 lane-per-bra, 1 warp (s and p class pairs)
     bool tuned = false;
     // device arrays
     ShellRec *d_shells = nullptr;
@@ -115,6 +133,7 @@ struct Plan {
     float2 *d_kblk2 = nullptr; // per 32 consecutive images: largest S, smallest pair exponent
     PpiRec *d_ppi = nullptr;
     PpiF *d_ppf = nullptr;
+    float *d_ppB = nullptr;  // |K| p^{-5/4} per primitive pair
     float *d_r1f = nullptr;
     SpairRec *d_spair = nullptr;
     int *d_spi_order = nullptr;
@@ -141,8 +160,8 @@ struct Plan {
     double *d_S = nullptr;  // raw-component overlap over the pair list
     size_t device_bytes = 0;
     Workspace ws;
+    RecipCache cache;
     PhaseTimer timer;
-    cublasHandle_t blas = nullptr;
     std::mutex build_mu;
     PlanDev dev() const;
 };
@@ -155,9 +174,12 @@ int compute_overlap_raw(Plan *p, cudaStream_t st);
 int build_times(Plan *p, double *ms, int *launches, int n);
 int build_counts(Plan *p, long long *counts, int n);
 int autotune(Plan *p, const double *D, cudaStream_t st, const char *cache_path, int *chosen);
+int set_schedule(Plan *P, const int *sched, int n);
 int ozaki_begin(Plan *P, cudaStream_t st);
-int ozaki_prepare_lowrank(Plan *P, cudaStream_t st);
-int ozaki_exchange_chunk(Plan *P, int m2, int S, cudaStream_t st);
+double ozaki_mma_flops(const Plan *P, const int dyn[3]);
+int ozaki_exchange_chunk(Plan *P, int chunk, const double *Mc, int m2, int S, cudaStream_t st);
+int cache_reciprocal(Plan *P, size_t max_bytes);
+void release_cache(Plan *P);
 int ozaki_setup_tc(Plan *P);
 int ozaki_finish(Plan *P, cudaStream_t st);
 struct Plan;

@@ -1,6 +1,6 @@
 // Real-space quartet kernels for bra class (0, 0) and ket class (1, 0) (generated by gen_units.py).
-#include "kernels.cuh"
 #include "launch.h"
+#include "real2.cuh"
 
 namespace jk {
 
@@ -9,16 +9,31 @@ void launch_real_q01(const RealLaunch &a)
     const int nb = a.b1 - a.b0, nk = a.k1 - a.k0;
     if (nb <= 0 || nk <= 0) return;
     if (a.list_pass) {
-        k_real_list<0, 0, 1, 0><<<152 * 8, kRealThreads, 0, a.st>>>(a.pl, a.big, a.nbig, a.cap, a.same, a.Dp, a.X, a.Y, a.cnt64);
+        k_real_list_w<0, 0, 1, 0><<<152 * 8, 32 * kWarpsPerBlock, 0, a.st>>>(a.pl, a.big, a.nbig, a.cap, a.same, a.Dp, a.X, a.Y,
+                                                                                  a.cnt64);
         return;
     }
-    dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+    if (a.variant == 0) {
+        dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+        if (a.fp32)
+            k_real<0, 0, 1, 0, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                               a.tau, a.Dpf, a.dmaxf, a.X, a.Y, a.cnt, a.big, a.nbig,
+                                                                               a.cap, a.ovf);
+        else
+            k_real<0, 0, 1, 0, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                                a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big, a.nbig,
+                                                                                a.cap, a.ovf);
+        return;
+    }
+    dim3 grid((nb + kWarpsPerBlock - 1) / kWarpsPerBlock, (nk + a.kchunk - 1) / a.kchunk);
     if (a.fp32)
-        k_real<0, 0, 1, 0, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode, a.tau,
-                                                                       a.Dpf, a.dmaxf, a.X, a.Y, a.cnt, a.big, a.nbig, a.cap, a.ovf);
+        k_real_w<0, 0, 1, 0, float><<<grid, 32 * kWarpsPerBlock, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
+                                                                                 a.mode, a.tau, a.Dpf, a.dmaxf, a.X, a.Y, a.cnt, a.big,
+                                                                                 a.nbig, a.cap, a.ovf);
     else
-        k_real<0, 0, 1, 0, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode, a.tau,
-                                                                        a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big, a.nbig, a.cap, a.ovf);
+        k_real_w<0, 0, 1, 0, double><<<grid, 32 * kWarpsPerBlock, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
+                                                                                  a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big,
+                                                                                  a.nbig, a.cap, a.ovf);
 }
 
 }  // namespace jk

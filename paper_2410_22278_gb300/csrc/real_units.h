@@ -25,6 +25,9 @@ void launch_real_q44(const RealLaunch &a);
 void launch_real_q45(const RealLaunch &a);
 void launch_real_q55(const RealLaunch &a);
 
+// class pairs of s and p shells have the warp kernels of real2.cuh as a second family
+inline bool real_has_warp_kernel(int cb, int ck) { return cb <= 2 && ck <= 2; }
+
 inline void launch_real(int cb, int ck, const RealLaunch &a)
 {
     switch (cb * 8 + ck) {

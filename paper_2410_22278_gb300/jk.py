@@ -35,7 +35,7 @@ EXPORTS = [
     "jk_plan_create", "jk_plan_info", "jk_pair_counts", "jk_plan_nbf", "jk_plan_destroy", "jk_build", "jk_build_host", "jk_build_times", "jk_build_counts", "jk_autotune", "jk_energy",
     "jk_energy_noalloc", "jk_one_electron",
     "jk_overlap", "jk_ewald_point_charges", "jk_server_create", "jk_submit", "jk_wait", "jk_server_destroy",
-    "jk_status_string", "jk_last_error", "jk_microbench_fma",
+    "jk_status_string", "jk_last_error", "jk_microbench_fma", "jk_plan_cache", "jk_plan_set_schedule",
 ]
 
 
@@ -93,9 +93,11 @@ def lib():
         L.jk_plan_destroy.argtypes = [vp]
         L.jk_plan_destroy.restype = None
         L.jk_build.argtypes = [vp, vp, vp, vp, vp]
+        L.jk_plan_cache.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
         L.jk_build_host.argtypes = [vp, dp, dp, dp, vp]
         L.jk_build_times.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         L.jk_build_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+        L.jk_plan_set_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         L.jk_autotune.argtypes = [vp, vp, vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
         L.jk_energy.argtypes = [vp, vp, vp, vp, dp, dp, vp]
         L.jk_energy_noalloc.argtypes = [vp, vp, vp, vp, dp, dp, vp]
@@ -194,6 +196,13 @@ class Plan:
     def nbf(self) -> int:
         return int(lib().jk_plan_nbf(self._h))
 
+    def cache(self, max_bytes: int) -> int:
+        """Keep the D-independent reciprocal data resident (jk_plan_cache);
+        returns its size in bytes (0 releases it)."""
+        b = ctypes.c_size_t()
+        _check(lib().jk_plan_cache(self._h, ctypes.c_size_t(int(max_bytes)), ctypes.byref(b)), "jk_plan_cache")
+        return int(b.value)
+
     def build(self, D_ptr: int, J_ptr: int, K_ptr: int, stream: int = 0):
         _check(lib().jk_build(self._h, D_ptr or None, J_ptr or None, K_ptr or None, stream or None), "jk_build")
 
@@ -226,23 +235,36 @@ class Plan:
         return out
 
     def autotune(self, D_ptr: int, stream: int = 0, cache_path: str = None):
-        """Tile shapes of the real-space kernels chosen by timing (jk_autotune)."""
-        chosen = (ctypes.c_int * 36)()
+        """Real-space schedule chosen by timing (jk_autotune): a list of 21
+        (family, kets) pairs, family 0 lane-per-bra, 1 warp."""
+        chosen = (ctypes.c_int * 42)()
         _check(lib().jk_autotune(self._h, D_ptr, stream or None, cache_path.encode() if cache_path else None, chosen),
                "jk_autotune")
-        return [c for c in chosen if c]
+        return [(chosen[2 * k], chosen[2 * k + 1]) for k in range(21)]
+
+    def set_schedule(self, sched):
+        """Set (family, kets) per class pair (jk_plan_set_schedule)."""
+        flat = (ctypes.c_int * (2 * len(sched)))(*[int(v) for pair in sched for v in pair])
+        _check(lib().jk_plan_set_schedule(self._h, flat, len(sched)), "jk_plan_set_schedule")
+
+    COUNTS = ["quartets_fp64", "quartets_fp32", "list_overflow", "density_rank", "flops_fp64", "flops_fp32", "lowrank",
+              "screen_fp64", "screen_fp32", "lane_terms_fp64", "lane_slots_fp64", "lane_terms_fp32", "lane_slots_fp32"]
 
     def build_counts(self):
         """(FP64 image quartets, FP32 image quartets) of the most recent build."""
-        c = (ctypes.c_longlong * 4)()
-        _check(lib().jk_build_counts(self._h, c, 4), "jk_build_counts")
-        return int(c[0]), int(c[1])
+        c = self.counters()
+        return c["quartets_fp64"], c["quartets_fp32"]
+
+    def counters(self) -> dict:
+        """Every work counter of the most recent build (jk_build_counts)."""
+        c = (ctypes.c_longlong * 13)()
+        _check(lib().jk_build_counts(self._h, c, 13), "jk_build_counts")
+        return {k: int(c[i]) for i, k in enumerate(self.COUNTS)}
 
     def real_space_flops(self):
         """(FP64, FP32) algorithmic flops of the real-space evaluation in the most recent build."""
-        c = (ctypes.c_longlong * 6)()
-        _check(lib().jk_build_counts(self._h, c, 6), "jk_build_counts")
-        return int(c[4]), int(c[5])
+        c = self.counters()
+        return c["flops_fp64"], c["flops_fp32"]
 
     def energy(self, D_ptr: int, J_ptr: int, K_ptr: int, stream: int = 0):
         ej, ek = ctypes.c_double(), ctypes.c_double()
