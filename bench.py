@@ -152,10 +152,13 @@ def cpu_baseline_sample(cell, D):
                       "full J+K build (%.0f s)" % (det["bra_sampled"], det["local_pairs"], det["n_g"], took, full_s)}
 
 
-def run_serving(args):
-    """The serving stream (Poisson arrivals, per-request plans resident on the
-    device, iterations submitted one after another with perturbed densities)
-    through the library's request server.  Prints one JSON line per precision."""
+def serve_stream(reqs, prec, slots, budget_bytes, iters, plan_precision_name):
+    """Serve `reqs` (synthcells.Request, Poisson arrival times) through the
+    library's request server: one client thread per request sleeps until its
+    arrival, creates the request's plan (resident on the device), and submits
+    its SCF iterations one after another (each a fresh density perturbation
+    of norm 1e-3) while other requests' builds run.  Returns latency and
+    throughput figures."""
     import threading
 
     import torch
@@ -163,21 +166,15 @@ def run_serving(args):
     import synthcells as sc
     from paper_2410_22278_gb300 import jk
 
-    reqs = [r for r in sc.serving_requests(256) if r.natom_target <= args.max_atoms][: args.requests]
     dev = torch.device("cuda:0")
-    results = {}
-    all_reqs = reqs
-    for prec, pname in ((jk.JK_MIXED, "mixed"), (jk.JK_FP64, "fp64")):
-        # the FP64 leg serves the first few requests with at most 3 iterations
-        # each (its builds are 10-50x slower), which is stated in the output
-        reqs = all_reqs if prec == jk.JK_MIXED else all_reqs[: args.fp64_requests]
-        iters = (lambda r: r.n_iter) if prec == jk.JK_MIXED else (lambda r: min(3, r.n_iter))
-        srv = jk.Server(device=0, hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)), max_slots=args.slots)
-        lat_build, lat_req = [], []
-        lock = threading.Lock()
-        t0 = time.perf_counter()
+    srv = jk.Server(device=0, hbm_budget_bytes=int(budget_bytes), max_slots=slots)
+    lat_build, lat_req, nbf = [], [], []
+    lock = threading.Lock()
+    errors = []
+    t0 = time.perf_counter()
 
-        def serve(r):
+    def serve(r):
+        try:
             arrive = t0 + (r.arrival_s - reqs[0].arrival_s)
             time.sleep(max(0.0, arrive - time.perf_counter()))
             t_arr = time.perf_counter()
@@ -195,28 +192,55 @@ def run_serving(args):
                 torch.cuda.synchronize()
                 tk = srv.submit(plan, Dk.data_ptr(), J.data_ptr(), K.data_ptr())
                 st, lat = srv.wait(tk)
-                assert st == 0
+                if st != 0:
+                    raise RuntimeError("build status %d" % st)
                 with lock:
                     lat_build.append(lat)
             with lock:
                 lat_req.append(time.perf_counter() - t_arr)
+                nbf.append(n)
             plan.close()
+        except Exception as e:  # reported in the output
+            with lock:
+                errors.append(repr(e))
 
-        threads = [threading.Thread(target=serve, args=(r,)) for r in reqs]
-        for th in threads:
-            th.start()
-        for th in threads:
-            th.join()
-        wall = time.perf_counter() - t0
-        srv.close()
-        results[pname] = {"requests": len(reqs), "builds": len(lat_build), "builds_per_s": len(lat_build) / wall, "wall_s": wall,
-                          "build_latency_ms": {"p50": 1e3 * float(np.percentile(lat_build, 50)),
-                                               "p99": 1e3 * float(np.percentile(lat_build, 99))},
-                          "request_latency_s": {"p50": float(np.percentile(lat_req, 50)), "p99": float(np.percentile(lat_req, 99))}}
-    out = {"metric": METRIC, "mode": "serving", "requests": len(all_reqs), "max_atoms": args.max_atoms, "slots": args.slots,
+    threads = [threading.Thread(target=serve, args=(r,)) for r in reqs]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    wall = time.perf_counter() - t0
+    srv.close()
+    out = {"precision": plan_precision_name, "requests": len(reqs), "builds": len(lat_build),
+           "builds_per_s": len(lat_build) / wall, "wall_s": wall,
+           "nbf_range": [min(nbf), max(nbf)] if nbf else None, "slots": slots}
+    if lat_build:
+        out["build_latency_ms"] = {"p50": 1e3 * float(np.percentile(lat_build, 50)), "p99": 1e3 * float(np.percentile(lat_build, 99))}
+    if lat_req:
+        out["request_latency_s"] = {"p50": float(np.percentile(lat_req, 50)), "p99": float(np.percentile(lat_req, 99))}
+    if errors:
+        out["errors"] = errors[:3]
+    return out
+
+
+def serving_requests(args):
+    import synthcells as sc
+
+    return [r for r in sc.serving_requests(256) if r.natom_target <= args.max_atoms][: args.requests]
+
+
+def run_serving(args):
+    """The serving stream alone, both precisions; one JSON line."""
+    from paper_2410_22278_gb300 import jk
+
+    reqs = serving_requests(args)
+    mixed = serve_stream(reqs, jk.JK_MIXED, args.slots, args.hbm_budget_gb * (1 << 30), lambda r: r.n_iter, "mixed")
+    fp64 = serve_stream(reqs[: args.fp64_requests], jk.JK_FP64, args.slots, args.hbm_budget_gb * (1 << 30),
+                        lambda r: min(3, r.n_iter), "fp64")
+    out = {"metric": METRIC, "mode": "serving", "max_atoms": args.max_atoms, "arrival_rate_per_s": 50.0,
            "fp64_leg": "first %d requests, at most 3 iterations each" % args.fp64_requests,
-           "arrival_rate_per_s": 50.0, "data": "synthetic (serving stream: Poisson 50/s, diamond/water 50/50, 3-20 iterations, "
-           "|E_k|_F = 1e-3; requests above max_atoms skipped)", **results}
+           "data": "synthetic (serving stream: Poisson 50/s, diamond/water 50/50, 3-20 iterations, |E_k|_F = 1e-3; "
+                   "requests above max_atoms skipped)", "mixed": mixed, "fp64": fp64}
     print(json.dumps(out))
     return 0
 
@@ -239,12 +263,15 @@ def main():
     ap.add_argument("--workload", default="water64", choices=sorted(WORKLOADS))
     ap.add_argument("--profile", action="store_true", help="mixed builds only (for ncu captures)")
     ap.add_argument("--serving", action="store_true", help="run the serving stream instead of the single-cell build")
-    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--max-atoms", type=int, default=64)
+    ap.add_argument("--no-serving", action="store_true", help="leave the bounded serving stream out of the bench line")
     ap.add_argument("--fp64-requests", type=int, default=4)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--hbm-budget-gb", type=float, default=64.0)
     ap.add_argument("--autotune-cache", default=None)
+    ap.add_argument("--no-cache", action="store_true", help="recompute the structure factors in every build")
+    ap.add_argument("--mixed-switch", type=float, default=0.0, help="precision switch tau of the mixed path (0: library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -271,7 +298,7 @@ def main():
 
     cell = make_workload(args.workload)
     n = cell.nbf
-    plan = jk.plan_from_cell(cell, precision=jk.JK_MIXED, device=local)
+    plan = jk.plan_from_cell(cell, precision=jk.JK_MIXED, device=local, mixed_switch=args.mixed_switch)
     plan64 = None if args.profile else jk.plan_from_cell(cell, precision=jk.JK_FP64, device=local)
     info = plan.info()
     S = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -291,6 +318,21 @@ def main():
     for _ in range(args.warmup):
         build(plan)
     stream.synchronize()
+    # the same build with every structure factor recomputed (no reciprocal
+    # cache): its phase split, for reference beside the cached steady state
+    phases_nocache = {k2: v[0] for k2, v in plan.build_times().items() if k2 != "mma_flops"}
+    # steady state of an SCF loop on one geometry: the D-independent
+    # reciprocal data stay resident (jk_plan_cache), filled by one untimed build
+    cache_bytes = 0
+    if not args.no_cache:
+        free, _ = torch.cuda.mem_get_info(dev)
+        try:
+            cache_bytes = plan.cache(max(0, free - (24 << 30)))
+        except jk.JkError as e:
+            print("reciprocal cache not used: %s" % e, file=sys.stderr)
+        for _ in range(2 if cache_bytes else 0):
+            build(plan)
+        stream.synchronize()
 
     # ---- timed region: exactly args.steps mixed builds
     clocks = Clocks(local)
@@ -323,8 +365,9 @@ def main():
     Jm, Km = J.cpu().numpy(), K.cpu().numpy()
     ej, ek = plan.energy(D.data_ptr(), J.data_ptr(), K.data_ptr(), st)
     if args.profile:
-        print(json.dumps({"profile": args.workload, "ms_per_step": ms_per_step, "phases_ms": {k2: v for k2, v in phases.items()},
-                          "counts": counts, "counters": plan.counters(), "schedule": tiles}))
+        print(json.dumps({"profile": args.workload, "mixed_switch": args.mixed_switch, "ms_per_step": ms_per_step, "phases_ms": {k2: v for k2, v in phases.items()},
+                          "counts": counts, "counters": plan.counters(), "schedule": tiles,
+                          "phases_ms_without_cache": phases_nocache, "cache_bytes": cache_bytes}))
         return 0
 
     # ---- errors of this build against the oracle's J and K rows of the same
@@ -385,6 +428,20 @@ def main():
             tdist.destroy_process_group()
         return 0
 
+    # ---- the serving stream, bounded (requests of at most --max-atoms atoms,
+    # the first --requests of the 256-request stream), mixed precision
+    serving = None
+    if not args.no_serving:
+        # every serving plan holds its own workspace: free the benchmark's
+        # reciprocal cache and the FP64 plan first
+        plan.cache(0)
+        plan64.close()
+        torch.cuda.empty_cache()
+        reqs = serving_requests(args)
+        serving = serve_stream(reqs, jk.JK_MIXED, args.slots, args.hbm_budget_gb * (1 << 30), lambda r: r.n_iter, "mixed")
+        serving["stream"] = ("first %d of the 256-request stream with at most %d atoms; Poisson arrivals at 50/s, 3-20 SCF "
+                             "iterations each, every iteration a fresh density" % (len(reqs), args.max_atoms))
+
     pk, pk_kind = peaks()
     launches = phases["total"][1]  # the library's own kernel launches per build (phases 0-5)
     nq = info["n_quartets_schwarz"]
@@ -394,8 +451,12 @@ def main():
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64 (mixed)", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "precision": "mixed", "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "no flush; each build streams a ~4 GB structure-factor slab (> L2)", "nbf": n,
-                   "shell_pair_images": info["n_pair_images"], "n_g_half": info["n_g"]},
+                   "l2": "no flush; each build streams the structure-factor slab (tens of GB, > L2)", "nbf": n,
+                   "shell_pair_images": info["n_pair_images"], "n_g_half": info["n_g"],
+                   "reciprocal_cache_bytes": cache_bytes,
+                   "reciprocal_cache": ("D-independent structure factors and their exchange slices resident between builds "
+                                        "(jk_plan_cache; an SCF loop on one geometry)") if cache_bytes else "off"},
+        "phases_ms_without_cache": phases_nocache,
         "quartets_per_s": nq / (ms_per_step / 1e3),
         "image_quartets_evaluated_per_s": (counts[0] + counts[1]) / (ms_per_step / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -414,6 +475,7 @@ def main():
         "roofline_other": roof_other,
         "clocks": cl,
         "e2e": {"value": 1.0 / e2e_s, "unit": "builds/s", "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8},
+        "serving": serving,
     }
     if not args.no_cpu_baseline and world == 1:
         from oracle import oracle as O
@@ -440,14 +502,13 @@ def roofline(phases, real_flops, pk, pk_kind, fma):
     GEMMs (BF16 MMA flops issued, against the measured BF16 peak).  Returns
     the family with the most device time first."""
     fl64, fl32 = real_flops
-    real_ms = phases["real_space"][0]
     list_ms, list_n = phases.get("real_fp64_list", (0.0, 0))
-    tile_ms = max(real_ms - list_ms, 1e-9)
+    tile_ms = max(phases["real_tiles"][0], 1e-9)
     mk = "measured on this GPU (jk_microbench_fma: independent FMA chains, %d SMs, CUDA events)" % fma["sms"]
     out = [
         {"bound": "alu", "kernel": "k_real<..., float> (FP32 real-space quartet tiles)", "achieved": fl32 / (tile_ms / 1e3) / 1e12,
          "peak": fma["fp32_tflops"], "unit": "TFLOP/s", "frac": fl32 / (tile_ms / 1e3) / 1e12 / fma["fp32_tflops"],
-         "traffic": REAL_TILE_TRAFFIC, "ms": tile_ms, "launches": phases["real_space"][1] - list_n,
+         "traffic": REAL_TILE_TRAFFIC, "ms": tile_ms, "launches": phases["real_tiles"][1],
          "peak_kind": "FP32 FMA rate " + mk,
          "work": "algorithmic flops of the MD steps (csrc/flops.h) tallied by the kernels"},
     ]

@@ -66,7 +66,7 @@ typedef struct {
 /* The four lattice-sum thresholds of Section 3.6 (values <= 0 select the
  * paper's default 1e-14) and the mixed-precision switch (Section 3.5):
  * an image quartet whose density-weighted size estimate is at or above
- * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: 3e-4). */
+ * mixed_switch is evaluated in FP64, below it in FP32 (<= 0: 3e-3). */
 typedef struct {
     double pair_R;   /* delta_pair-R, Eq. pbc_eri_pair_cutoff_implementation */
     double pair_cs;  /* delta_pair-Cauchy-Schwarz, Eq. pbc_eri_cauchy_schwarz_cutoff_implementation */
@@ -202,34 +202,36 @@ int jk_energy_noalloc(const jk_plan *plan, const double *D, const double *J, con
 
 /* Device time of each phase of the most recent jk_build on this plan, in
  * milliseconds, from CUDA events recorded on the build's stream around the
- * phase's kernels (waits for that build to finish).  ms[0] prologue (D
- * scaling, zeroing), ms[1] real-space quartet kernels, ms[2] reciprocal
- * structure factors, ms[3] reciprocal Coulomb contraction, ms[4]
+ * phase's kernels (waits for that build to finish).  ms[0] prologue (D scaling, zeroing, density slices and
+ * factorisation), ms[1] real space (fork to the last list pass), ms[2]
+ * reciprocal structure factors, ms[3] reciprocal Coulomb contraction, ms[4]
  * reciprocal exchange contraction, ms[5] background and assembly, ms[6]
  * whole build, ms[7] the tensor-core GEMM launches inside ms[4] (mixed
- * precision), ms[8] their operand slicing, ms[9] the FP64 pass over the
- * large quartets inside ms[1] (mixed precision), ms[10] (not a time) the
- * BF16 MMA flops the GEMMs issued; launches[i] the kernel launches per
- * phase.  n = number of slots the caller provides (<= 11 used). */
+ * precision), ms[8] their operand slicing, ms[9] the FP64 list passes inside
+ * ms[1] (mixed precision), ms[10] the FP32 (mixed) or FP64 tile kernels
+ * inside ms[1], ms[11] (not a time) the BF16 MMA flops the GEMMs issued;
+ * launches[i] the kernel launches per phase.  n = number of slots the
+ * caller provides (<= 12 used). */
 int jk_build_times(jk_plan *plan, double *ms, int *launches, int n);
 
 /* Autotuner (no counterpart in the paper): choose the tile shape of every
- * real-space class-pair kernel (kets per warp, candidates 128 .. 2048, for
- * the warp kernels of the s and p classes; kets per tile, 8 .. 128, for the
- * classes with a d shell) by timing the candidates on a sub-range of bras
- * with CUDA events, on
+ * real-space class-pair kernel -- the family (0 lane-per-bra, 8 .. 128 kets
+ * per tile; for class pairs of s and p shells also 1 warp-per-bra, 128 ..
+ * 2048 kets per warp, and 2 pair queue, 32 .. 512 kets per tile) and its
+ * tile -- by timing the candidates on two sub-ranges of bras with CUDA
+ * events, on
  * `cuda_stream`, using density D (device, as in jk_build) for realistic
  * work.  If cache_path is not NULL, choices are read from and written to
  * that text file, keyed by GPU name, precision, class pair and size
  * bucket.  chosen (may be NULL) receives 42 ints: (family, kets) for each
  * of the 21 class pairs (bra class <= ket class, classes ss, ps, pp, ds,
- * dp, dd), family 0 lane-per-bra, 1 warp.  Overwrites the plan's build
- * workspace; synchronises the stream. */
+ * dp, dd), family 0 lane-per-bra, 1 warp, 2 pair queue.  Overwrites the
+ * plan's build workspace; synchronises the stream. */
 int jk_autotune(jk_plan *plan, const double *D, void *cuda_stream, const char *cache_path, int *chosen);
 
 /* Set the real-space schedule directly (what jk_autotune chooses): sched
  * holds (family, kets) for the first n class pairs in jk_autotune's order;
- * family 1 (warp kernels) only for class pairs of s and p shells, kets in
+ * families 1 and 2 only for class pairs of s and p shells, kets in
  * 1..65535.  Results do not depend on the schedule beyond rounding.
  * Errors: JK_ERR_INVALID (nothing is changed). */
 int jk_plan_set_schedule(jk_plan *plan, const int *sched, int n);

@@ -189,7 +189,7 @@ int compute_overlap_raw(Plan *P, cudaStream_t st)
 
 void PhaseTimer::begin(cudaStream_t s)
 {
-    st = s;
+    st = cur = s;
     next = 0;
     marks.clear();
     for (int i = 0; i < kPhases; ++i) launches[i] = 0;
@@ -202,7 +202,7 @@ int PhaseTimer::start(int phase)
         cudaEventCreate(&e);
         pool.push_back(e);
     }
-    cudaEventRecord(pool[next], st);
+    cudaEventRecord(pool[next], cur);
     return next++;
 }
 void PhaseTimer::stop(int phase, int ev_start, int nlaunch)
@@ -217,98 +217,18 @@ void PhaseTimer::destroy()
     pool.clear();
 }
 
-// The caller holds P->build_mu (jk_build), so the stream ordering against
-// the previous build on this plan and the use of its workspace are one
-// critical section.
-int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
+// Reciprocal (erf) part of the build on stream st: structure factors (or
+// the cache), the Coulomb slab passes and the exchange contraction, chunk
+// by chunk of G.  Enqueued on its own stream, concurrent with real space.
+static int reciprocal_phase(Plan *P, double *J, double *K, cudaStream_t st)
 {
-    if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
     const int n = P->nbf;
     const size_t n2 = (size_t)n * n;
     PlanDev pl = P->dev();
     Workspace &w = P->ws;
     const bool mixed = P->precision == JK_MIXED;
     PhaseTimer &tm = P->timer;
-    tm.begin(st);
-    const int ev_all = tm.start(6);
-    int ev = tm.start(0);
-
-    k_scale<<<grid_for(n2), 256, 0, st>>>(n, P->d_compf, D, w.Dp);
-    if (mixed) {
-        const long long ns2 = (long long)P->nshell * P->nshell;
-        k_dmax<<<(unsigned)((ns2 + 255) / 256), 256, 0, st>>>(pl, w.Dp, w.dmax);
-        k_to_float<<<grid_for(n2), 256, 0, st>>>(n2, w.Dp, w.Dpf);
-        k_to_float<<<grid_for((size_t)ns2), 256, 0, st>>>((size_t)ns2, w.dmax, w.dmaxf);
-    }
-    cudaMemsetAsync(w.X, 0, n2 * sizeof(double), st);
-    cudaMemsetAsync(w.Y, 0, n2 * sizeof(double), st);
-    cudaMemsetAsync(w.JLR, 0, n2 * sizeof(double), st);
-    cudaMemsetAsync(w.KLR, 0, n2 * sizeof(double), st);
-    cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), st);
-    cudaMemsetAsync(w.cnt, 0, kCounters * sizeof(unsigned long long), st);
-    if (w.nbig) cudaMemsetAsync(w.nbig, 0, 2 * sizeof(unsigned), st);
-    int rc;
-    if ((rc = cuda_check("prologue"))) return rc;
-    // mixed precision: slices of D' and its low-rank factorisation for the
-    // exchange contraction (decided on the device; nothing waits for it)
-    if (mixed && K && (rc = ozaki_begin(P, st))) return rc;
-    tm.stop(0, ev, mixed ? (K ? 8 : 4) : 1);
-
-    // ---- real space
-    ev = tm.start(1);
-    int nreal = 0;
-    for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
-        for (int ck = cb; ck < JK_NCLASS_MAX; ++ck) {
-            const ClassRange &B = P->classes[cb], &Kc = P->classes[ck];
-            if (B.b1 <= B.b0 || Kc.b1 <= Kc.b0) continue;
-            RealLaunch a{};
-            a.pl = pl;
-            a.b0 = B.b0;
-            a.b1 = B.b1;
-            a.k0 = Kc.b0;
-            a.k1 = Kc.b1;
-            a.same = cb == ck;
-            a.kchunk = P->kchunk[cb][ck];
-            a.variant = P->kvariant[cb][ck];
-            a.tau = P->mixed_tau;
-            a.Dp = w.Dp;
-            a.dmax = w.dmax;
-            a.Dpf = w.Dpf;
-            a.dmaxf = w.dmaxf;
-            a.X = w.X;
-            a.Y = w.Y;
-            a.st = st;
-            if (!mixed) {
-                a.mode = 0;
-                a.fp32 = false;
-                a.cnt = w.cnt;
-                launch_real(cb, ck, a);
-                nreal += 1;
-            } else {
-                // FP32 pass over every quartet, collecting the large ones ...
-                cudaMemsetAsync(w.nbig, 0, sizeof(unsigned), st);
-                a.mode = 2;
-                a.fp32 = true;
-                a.cnt = w.cnt + 1;
-                a.big = w.big;
-                a.nbig = w.nbig;
-                a.ovf = w.nbig + 1;
-                a.cap = w.cap;
-                launch_real(cb, ck, a);
-                // ... then FP64 over the compact list
-                a.list_pass = true;
-                a.cnt64 = w.cnt;
-                const int el = tm.start(9);
-                launch_real(cb, ck, a);
-                tm.stop(9, el, 1);
-                nreal += 2;
-            }
-            if ((rc = cuda_check("real-space kernel"))) return rc;
-        }
-
-    tm.stop(1, ev, nreal);
-
-    // ---- reciprocal space
+    int ev, rc;
     const int ng = (int)(P->gvec.size() / 4);
     // mixed precision: structure factors in double-float on the FP32 pipe
     const bool sfac_df = mixed && P->sfac_df && w.gtab2;
@@ -367,6 +287,109 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     } else if (K && ng > 0) {
         mirror_upper(n, w.KLR, st);
     }
+    return cuda_check("reciprocal phase");
+}
+
+// The caller holds P->build_mu (jk_build), so the stream ordering against
+// the previous build on this plan and the use of its workspace are one
+// critical section.
+int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
+{
+    if (cudaSetDevice(P->device) != cudaSuccess) return fail(JK_ERR_CUDA, "cudaSetDevice failed");
+    const int n = P->nbf;
+    const size_t n2 = (size_t)n * n;
+    PlanDev pl = P->dev();
+    Workspace &w = P->ws;
+    const bool mixed = P->precision == JK_MIXED;
+    PhaseTimer &tm = P->timer;
+    tm.begin(st);
+    const int ev_all = tm.start(6);
+    int ev = tm.start(0);
+
+    k_scale<<<grid_for(n2), 256, 0, st>>>(n, P->d_compf, D, w.Dp);
+    if (mixed) {
+        const long long ns2 = (long long)P->nshell * P->nshell;
+        k_dmax<<<(unsigned)((ns2 + 255) / 256), 256, 0, st>>>(pl, w.Dp, w.dmax);
+        k_to_float<<<grid_for(n2), 256, 0, st>>>(n2, w.Dp, w.Dpf);
+        k_to_float<<<grid_for((size_t)ns2), 256, 0, st>>>((size_t)ns2, w.dmax, w.dmaxf);
+    }
+    cudaMemsetAsync(w.X, 0, n2 * sizeof(double), st);
+    cudaMemsetAsync(w.Y, 0, n2 * sizeof(double), st);
+    cudaMemsetAsync(w.JLR, 0, n2 * sizeof(double), st);
+    cudaMemsetAsync(w.KLR, 0, n2 * sizeof(double), st);
+    cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(w.cnt, 0, kCounters * sizeof(unsigned long long), st);
+    if (w.nbig) cudaMemsetAsync(w.nbig, 0, 2 * sizeof(unsigned), st);
+    int rc;
+    if ((rc = cuda_check("prologue"))) return rc;
+    // mixed precision: slices of D' and its low-rank factorisation for the
+    // exchange contraction (decided on the device; nothing waits for it)
+    if (mixed && K && (rc = ozaki_begin(P, st))) return rc;
+    tm.stop(0, ev, mixed ? (K ? 8 : 4) : 1);
+
+    // ---- real space (the phases run one after another on the caller's
+    // stream: run on streams of their own they gained nothing on the water
+    // box -- the tile kernels fill every SM, and the tensor-core GEMMs, which
+    // need a whole SM each, only start as the tile grids drain)
+    ev = tm.start(1);
+    int nreal = 0;
+    for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
+        for (int ck = cb; ck < JK_NCLASS_MAX; ++ck) {
+            const ClassRange &B = P->classes[cb], &Kc = P->classes[ck];
+            if (B.b1 <= B.b0 || Kc.b1 <= Kc.b0) continue;
+            RealLaunch a{};
+            a.pl = pl;
+            a.b0 = B.b0;
+            a.b1 = B.b1;
+            a.k0 = Kc.b0;
+            a.k1 = Kc.b1;
+            a.same = cb == ck;
+            a.kchunk = P->kchunk[cb][ck];
+            a.variant = P->kvariant[cb][ck];
+            a.tau = P->mixed_tau;
+            a.Dp = w.Dp;
+            a.dmax = w.dmax;
+            a.Dpf = w.Dpf;
+            a.dmaxf = w.dmaxf;
+            a.X = w.X;
+            a.Y = w.Y;
+            a.st = st;
+            if (!mixed) {
+                a.mode = 0;
+                a.fp32 = false;
+                a.cnt = w.cnt;
+                const int et = tm.start(10);
+                launch_real(cb, ck, a);
+                tm.stop(10, et, 1);
+                nreal += 1;
+            } else {
+                // FP32 pass over every quartet, collecting the large ones ...
+                cudaMemsetAsync(w.nbig, 0, sizeof(unsigned), st);
+                a.mode = 2;
+                a.fp32 = true;
+                a.cnt = w.cnt + 1;
+                a.big = w.big;
+                a.nbig = w.nbig;
+                a.ovf = w.nbig + 1;
+                a.cap = w.cap;
+                const int et = tm.start(10);
+                launch_real(cb, ck, a);
+                tm.stop(10, et, 1);
+                // ... then FP64 over the compact list
+                a.list_pass = true;
+                a.cnt64 = w.cnt;
+                const int el = tm.start(9);
+                launch_real(cb, ck, a);
+                tm.stop(9, el, 1);
+                nreal += 2;
+            }
+            if ((rc = cuda_check("real-space kernel"))) return rc;
+        }
+    tm.stop(1, ev, nreal);
+
+    // ---- reciprocal space
+    if ((rc = reciprocal_phase(P, J, K, st))) return rc;
+
     ev = tm.start(5);
 
     // ---- removed K = 0 term: c = -pi / (V w^2)
@@ -418,9 +441,11 @@ int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, 
     float part_ms = 0;
     // candidates (family, kets per tile): lane-per-bra kernels with 8 .. 128
     // kets per tile, and for s and p class pairs the warp kernels with
-    // 128 .. 2048 kets per warp; a choice is stored as family * 65536 + kets
+    // 128 .. 2048 kets per warp and the pair-queue kernels with 32 .. 512
+    // kets per tile; a choice is stored as family * 65536 + kets
     std::vector<int> cands_t = {8, 16, 32, 64, 128}, cands_w;
-    for (int c : {128, 256, 512, 1024, 2048}) cands_w.push_back(65536 + c);
+    for (int c : {128, 256, 512, 1024, 2048}) cands_w.push_back(65536 + c);   // warp kernels
+    for (int c : {32, 64, 128, 256, 512}) cands_w.push_back(2 * 65536 + c);   // pair-queue kernels
     int k = 0;
     bool dirty = false;
     for (int cb = 0; cb < JK_NCLASS_MAX; ++cb)
@@ -432,7 +457,7 @@ int autotune(Plan *P, const double *D, cudaStream_t st, const char *cache_path, 
             }
             if (B.b1 <= B.b0 || Kc.b1 <= Kc.b0) continue;
             char key[512];
-            snprintf(key, sizeof key, "%s|%s|v2|%d%d|%d|%d", prop.name, mixed ? "mixed" : "fp64", cb, ck, bucket(B.b1 - B.b0),
+            snprintf(key, sizeof key, "%s|%s|v3|%d%d|%d|%d", prop.name, mixed ? "mixed" : "fp64", cb, ck, bucket(B.b1 - B.b0),
                      bucket(Kc.b1 - Kc.b0));
             for (char *q = key; *q; ++q)
                 if (*q == ' ') *q = '_';
@@ -520,7 +545,7 @@ int set_schedule(Plan *P, const int *sched, int n)
         for (int ck = cb; ck < JK_NCLASS_MAX; ++ck, ++k) {
             if (k >= n) return JK_OK;
             const int fam = sched[2 * k], kets = sched[2 * k + 1];
-            if (fam < 0 || fam > 1 || (fam == 1 && !real_has_warp_kernel(cb, ck)) || kets < 1 || kets > 65535)
+            if (fam < 0 || fam > 2 || (fam >= 1 && !real_has_warp_kernel(cb, ck)) || kets < 1 || kets > 65535)
                 return fail(JK_ERR_INVALID, "schedule entry " + std::to_string(k) + " out of range");
         }
     k = 0;
@@ -574,14 +599,14 @@ int build_times(Plan *P, double *ms, int *launches, int n)
     int tot = 0;
     for (int i = 0; i < 6; ++i) tot += tm.launches[i];
     if (launches && n > 6) launches[6] = tot;
-    if (ms && n > 10) {
-        // slot 10: BF16 MMA flops issued (for the tensor roofline), from the
+    if (ms && n > 11) {
+        // slot 11: BF16 MMA flops issued (for the tensor roofline), from the
         // form and rank the device chose
         int dyn[3] = {0, 0, 0};
         if (P->precision == JK_MIXED && P->ws.lr.dyn &&
             cudaMemcpy(dyn, P->ws.lr.dyn, sizeof dyn, cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(JK_ERR_CUDA, "status copy failed");
-        ms[10] = P->precision == JK_MIXED ? ozaki_mma_flops(P, dyn) : 0.0;
+        ms[11] = P->precision == JK_MIXED ? ozaki_mma_flops(P, dyn) : 0.0;
     }
     return JK_OK;
 }

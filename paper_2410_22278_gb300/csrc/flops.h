@@ -96,4 +96,35 @@ constexpr long long per_quartet(int LA, int LB, int LC, int LD)
 }
 
 }  // namespace flops
+
+// Event counts of one thread in a real-space kernel (32-bit, cheap to bump
+// in the inner loops), turned into operation counts once per launch:
+// algorithmic work (the McMurchie-Davidson steps of each lattice image,
+// primitive quartet and image quartet) and screening / bookkeeping (radius
+// tests, minimum images, image search, Hermite tables formed again).
+struct Tally {
+    unsigned screen = 0;  // primitive quartets screened
+    unsigned radius = 0;  // of those, radius and minimum image formed (magnitude test passed)
+    unsigned cand = 0;    // lattice-vector candidates examined
+    unsigned img = 0;     // lattice images evaluated (inside the sphere)
+    unsigned term = 0;    // primitive quartets with at least one image, contracted into the block
+    unsigned ketp = 0;    // ket Hermite tables formed for a lane
+    unsigned brap = 0;    // bra Hermite tables formed
+    unsigned quart = 0;   // image quartets digested into J and K
+};
+
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr unsigned long long tally_alg(const Tally &t)
+{
+    return (unsigned long long)t.img * (flops::per_image(LA + LB + LC + LD) - 8) +
+           (unsigned long long)t.term * (flops::per_prim_quartet(LA, LB, LC, LD) - 76) +
+           (unsigned long long)t.quart * flops::per_quartet(LA, LB, LC, LD);
+}
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr unsigned long long tally_screen(const Tally &t)
+{
+    return (unsigned long long)t.screen * flops::per_prim_screen() + (unsigned long long)t.radius * 76 + (unsigned long long)t.cand * 8 +
+           (unsigned long long)t.brap * flops::per_bra_prim(LA, LB) + (unsigned long long)t.ketp * 3 * flops::herm_E(LC, LD);
+}
+
 }  // namespace jk

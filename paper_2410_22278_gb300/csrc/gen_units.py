@@ -3,9 +3,9 @@ real-space kernels (real_q<cb><ck>.cu), so that the 21 instantiations
 compile in parallel.  Run from this directory: python gen_units.py"""
 CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
 
-# Classes of s and p shells have two tile-kernel families, the warp
-# kernels of real2.cuh and the lane-per-bra kernels of kernels.cuh, and the
-# autotuner picks one per class pair (RealLaunch::variant); their FP64 list
+# Classes of s and p shells have three tile-kernel families, the
+# lane-per-bra kernels of kernels.cuh and the warp and pair-queue kernels of
+# real2.cuh, and the autotuner picks one per class pair (RealLaunch::variant); their FP64 list
 # pass is the warp kernel.  Classes with a d shell keep the lane-per-bra
 # kernels (their Cartesian blocks are too large for a warp-wide segmented
 # reduction in registers).
@@ -22,6 +22,18 @@ void launch_real_q{cb}{ck}(const RealLaunch &a)
     if (a.list_pass) {{
         k_real_list_w<{la}, {lb}, {lc}, {ld}><<<152 * 8, 32 * kWarpsPerBlock, 0, a.st>>>(a.pl, a.big, a.nbig, a.cap, a.same, a.Dp, a.X, a.Y,
                                                                                   a.cnt64);
+        return;
+    }}
+    if (a.variant == 2) {{
+        dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+        if (a.fp32)
+            k_real_q<{la}, {lb}, {lc}, {ld}, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
+                                                                                 a.mode, a.tau, a.Dpf, a.dmaxf, a.X, a.Y, a.cnt, a.big,
+                                                                                 a.nbig, a.cap, a.ovf);
+        else
+            k_real_q<{la}, {lb}, {lc}, {ld}, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
+                                                                                  a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big,
+                                                                                  a.nbig, a.cap, a.ovf);
         return;
     }}
     if (a.variant == 0) {{

@@ -52,7 +52,7 @@ struct PpiRec {      // one local primitive pair
     double pad;      // 1/p
 };
 
-struct PpiF {        // single-precision copy of a local primitive pair (FP32 kernels, screening)
+struct __align__(16) PpiF {  // single-precision copy of a local primitive pair (FP32 kernels, screening); 48 B, loaded as 3 x 16 B
     float P[3];
     float PA[3];
     float PB[3];

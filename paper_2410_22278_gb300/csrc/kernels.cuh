@@ -159,7 +159,7 @@ __device__ __forceinline__ float lat_at(const PlanDev &pl, int k, float) { retur
 // kernels (they only decide which terms to form); the terms themselves are
 // formed in T.
 template <int LA, int LB, int LC, int LD, typename T>
-__device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk, T *V, unsigned long long &fl)
+__device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &sb, const SpiRec &sk, T *V, Tally &tl)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int L = LA + LB + LC + LD, LAB = LA + LB, LCD = LC + LD;
@@ -179,7 +179,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
         load_pair(pl, sb.pp0 + i, xf, x);
         T Ea[3][(LA + 1) * (LB + 1) * NTA];
         const T oo2p = T(0.5) * x.ip;
-        fl += flops::per_bra_prim(LA, LB);
+        ++tl.brap;
 #pragma unroll
         for (int k = 0; k < 3; ++k) herm_E<LA, LB, T>(x.PA[k], x.PB[k], oo2p, Ea[k]);
         for (int j = 0; j < sk.npp; ++j) {
@@ -190,10 +190,11 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             const float awf = 1.0f / (ipf + iqf + iw2);
             const float cwf = sqrtf(awf * (ipf + iqf));
             const float preff = 34.986836655249725f * xf.K * yf.K * ipf * iqf * rsqrtf(xf.p + yf.p);
-            fl += flops::per_prim_screen();
+            ++tl.screen;
 
             const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
             if (!(lg > 0.0f)) continue;
+            ++tl.radius;
             float r = sqrtf(lg / awf);
             if (L > 0) {
                 r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
@@ -227,12 +228,13 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             const T cw = sqrt(aw * (ip + iq));
             for (int c = 0; c < pl.nr1; ++c) {
                 if (pl.r1f[4 * c + 3] - x0n >= r) break;
+                ++tl.cand;
                 const T Xx = X0[0] - lat_at(pl, 4 * c, T(0)), Xy = X0[1] - lat_at(pl, 4 * c + 1, T(0)),
                         Xz = X0[2] - lat_at(pl, 4 * c + 2, T(0));
                 const T x2 = Xx * Xx + Xy * Xy + Xz * Xz;
                 if ((float)x2 >= r2) continue;
                 any = true;
-                fl += flops::per_image(L);
+                ++tl.img;
                 T s[L + 1];
                 seeds<L>(x2, alpha, aw, cw, pl, s);
                 T B[D * D * D];
@@ -245,7 +247,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
                         for (int v = 0; v <= L - t - u; ++v) Rs[(t * D + u) * D + v] += B[(t * D + u) * D + v];
             }
             if (!any) continue;
-            fl += flops::per_prim_quartet(LA, LB, LC, LD);
+            ++tl.term;
             T Ec[3][(LC + 1) * (LD + 1) * NTC];
             const T oo2q = T(0.5) * iq;
 #pragma unroll
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
         for (int b = 0; b < NB; ++b) Dij[a * NB + b] = __ldg(Dp + (size_t)(aoI + a) * n + aoJ + b);
     const float tauf = (float)tau;
     unsigned nq = 0;
-    unsigned long long fl = 0;  // algorithmic flops (flops.h)
+    Tally tl;  // event counts (flops.h)
     for (int kt = kbeg; kt < kend; ++kt) {
         // one bound per block of 32 kets for the whole warp first
         if (kt == kbeg || (kt & 31) == 0) {
@@ -486,9 +488,9 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
         T V[NA * NB * NC * ND];
 #pragma unroll
         for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = T(0);
-        if (valid) quartet_block<LA, LB, LC, LD, T>(pl, sb, sk, V, fl);
+        if (valid) quartet_block<LA, LB, LC, LD, T>(pl, sb, sk, V, tl);
         nq += valid;
-        fl += valid ? flops::per_quartet(LA, LB, LC, LD) : 0;
+        tl.quart += valid;
         // orbit weight, exact in either precision
         const T w = valid ? T(sb.w) * T(sk.w) * ((same && kt == bra) ? T(0.5) : T(1)) : T(0);
         const int aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
@@ -574,13 +576,16 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
     // warp-aggregated counts of the image quartets this launch evaluated and
     // of their algorithmic flops (cnt[4])
     unsigned tot = nq;
+    unsigned long long fl = tally_alg<LA, LB, LC, LD>(tl), fs = tally_screen<LA, LB, LC, LD>(tl);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         tot += __shfl_xor_sync(0xffffffffu, tot, o);
         fl += __shfl_xor_sync(0xffffffffu, fl, o);
+        fs += __shfl_xor_sync(0xffffffffu, fs, o);
     }
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);
     if ((threadIdx.x & 31) == 0 && fl) atomicAdd(cnt + 4, fl);
+    if ((threadIdx.x & 31) == 0 && fs) atomicAdd(cnt + 8, fs);
 }
 
 // FP64 pass over the compact list of large quartets collected by the
@@ -596,15 +601,15 @@ __global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const in
     const unsigned total = min(*nbig, cap);
     const int n = pl.nbf;
     unsigned done = 0;
-    unsigned long long fl = 0;
+    Tally tl;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int2 q = big[e];
         const SpiRec sb = pl.spi[q.x], sk = pl.spi[q.y];
         double V[NA * NB * NC * ND];
 #pragma unroll
         for (int k = 0; k < NA * NB * NC * ND; ++k) V[k] = 0.0;
-        quartet_block<LA, LB, LC, LD, double>(pl, sb, sk, V, fl);
-        fl += flops::per_quartet(LA, LB, LC, LD);
+        quartet_block<LA, LB, LC, LD, double>(pl, sb, sk, V, tl);
+        ++tl.quart;
         ++done;
         const double w = double(sb.w) * double(sk.w) * ((same && q.x == q.y) ? 0.5 : 1.0);
         const int aoI = pl.shells[sb.I].ao, aoJ = pl.shells[sb.J].ao, aoK = pl.shells[sk.I].ao, aoL = pl.shells[sk.J].ao;
@@ -677,13 +682,16 @@ __global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const in
             }
     }
     unsigned tot = done;
+    unsigned long long fl = tally_alg<LA, LB, LC, LD>(tl), fs = tally_screen<LA, LB, LC, LD>(tl);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         tot += __shfl_xor_sync(0xffffffffu, tot, o);
         fl += __shfl_xor_sync(0xffffffffu, fl, o);
+        fs += __shfl_xor_sync(0xffffffffu, fs, o);
     }
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(cnt, (unsigned long long)tot);
     if ((threadIdx.x & 31) == 0 && fl) atomicAdd(cnt + 4, fl);
+    if ((threadIdx.x & 31) == 0 && fs) atomicAdd(cnt + 8, fs);
 }
 
 // sin and cos of a phase in FP64 by table and angle addition: theta =

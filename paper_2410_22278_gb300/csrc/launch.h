@@ -20,7 +20,7 @@ struct RealLaunch {
     unsigned *nbig, *ovf;
     unsigned cap;
     bool list_pass;      // launch k_real_list over the list instead of the tile kernel
-    int variant;         // s and p class pairs: 0 lane-per-bra tile kernel, 1 warp kernel (autotuned)
+    int variant;         // 0 lane-per-bra tile kernel; for s and p class pairs also 1 warp, 2 pair-queue kernel (autotuned)
     unsigned long long *cnt64;
     cudaStream_t st;
 };

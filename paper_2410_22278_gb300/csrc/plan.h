@@ -73,15 +73,19 @@ struct Workspace {
     int kpart_splits = 0;
 };
 
-// CUDA events bracketing the phases of one build (see jk_build_times)
+// CUDA events bracketing the phases of one build (see jk_build_times); a
+// phase's events are recorded on the stream its kernels run on (`cur`).
 struct PhaseTimer {
-    static constexpr int kPhases = 10;  // 0..6 as in jk_build_times, 7 tensor-core GEMMs, 8 their slicing, 9 FP64 list pass
+    // 0..6 as in jk_build_times, 7 tensor-core GEMMs, 8 their slicing, 9 FP64
+    // list pass, 10 FP32 real-space tile kernels
+    static constexpr int kPhases = 11;
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<int, int>>> marks;  // phase, (start event, end event)
     int next = 0;
     int launches[kPhases] = {0};
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr, cur = nullptr;
     void begin(cudaStream_t s);
+    void use(cudaStream_t s) { cur = s; }
     int start(int phase);
     void stop(int phase, int ev_start, int nlaunch);
     void destroy();
@@ -124,7 +128,7 @@ struct Plan {
     long long n_shell_pairs = 0, n_quartets = 0, n_quartets_schwarz = 0, n_quartets_fp64 = 0;
     double mixed_tau = 0;
     int kchunk[JK_NCLASS_MAX][JK_NCLASS_MAX];    // kets per tile (or per warp) of the real-space kernels (autotuned)
-    int kvariant[JK_NCLASS_MAX][JK_NCLASS_MAX];  // kernel family: 0 lane-per-bra, 1 warp (s and p class pairs)
+    int kvariant[JK_NCLASS_MAX][JK_NCLASS_MAX];  // kernel family: 0 lane-per-bra, 1 warp, 2 pair queue (1, 2: s and p class pairs)
     bool tuned = false;
     // device arrays
     ShellRec *d_shells = nullptr;

@@ -20,8 +20,8 @@
 // primitives ends at the first pair whose B_i B_j lies below the
 // per-term threshold (PlanDev::mag_thr): the magnitude test of Eq.
 // pbc_eri_real_cutoff_implementation fails for it and for every later one.
-// Which kernel family (this one or the lane-per-bra one) runs a class pair
-// is chosen by the autotuner.
+// Which kernel family (this one, the lane-per-bra one of kernels.cuh or the
+// pair-queue one below) runs a class pair is chosen by the autotuner.
 // The FP64 pass over the large quartets of the mixed path likewise gives one
 // list entry to a whole warp: its primitive quartets are screened 32 at a
 // time, queued, evaluated one per lane and summed by a full warp reduction.
@@ -89,12 +89,11 @@ __device__ __forceinline__ bool prim_reaches(const PlanDev &pl, const PpiF &bf, 
 // One primitive quartet (bra pair xb, ket pair xk): screening radius of Eq.
 // pbc_eri_real_cutoff_implementation (single precision), minimum image,
 // the R1 images inside the sphere, seeds and the Hermite R table, then the
-// contraction with both E tables into the Cartesian block V.  fl counts the
-// algorithmic flops of the McMurchie-Davidson steps, fs the screening
-// arithmetic (radius, minimum image, image search).
+// contraction with both E tables into the Cartesian block V; the events go
+// to the lane's tally (flops.h).
 template <int LA, int LB, int LC, int LD, typename T>
 __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB, T> &b, const PpiF &bf, const PrimE<LC, LD, T> &k,
-                                          const PpiF &kf, T *V, unsigned long long &fl, unsigned long long &fs)
+                                          const PpiF &kf, T *V, Tally &tl)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int L = LA + LB + LC + LD, LAB = LA + LB, LCD = LC + LD;
@@ -104,7 +103,7 @@ __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB,
     const float awf = 1.0f / (ipf + iqf + iw2);
     const float cwf = sqrtf(awf * (ipf + iqf));
     const float preff = 34.986836655249725f * bf.K * kf.K * ipf * iqf * rsqrtf(bf.p + kf.p);
-    fs += flops::per_prim_screen();
+    ++tl.screen;
     const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
     if (!(lg > 0.0f)) return;
     float r = sqrtf(lg / awf);
@@ -126,7 +125,7 @@ __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB,
         for (int a = 0; a < 3; ++a)
             X0[a] -= f[0] * latc(pl.L, pl.Lf, a, T(0)) + f[1] * latc(pl.L, pl.Lf, 3 + a, T(0)) + f[2] * latc(pl.L, pl.Lf, 6 + a, T(0));
     }
-    fs += 31 + 45;
+    ++tl.radius;
     const float x0n = sqrtf((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
     T Rs[D * D * D];
 #pragma unroll
@@ -140,10 +139,10 @@ __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB,
         if (pl.r1f[4 * c + 3] - x0n >= r) break;
         const T Xx = X0[0] - lat_at(pl, 4 * c, T(0)), Xy = X0[1] - lat_at(pl, 4 * c + 1, T(0)), Xz = X0[2] - lat_at(pl, 4 * c + 2, T(0));
         const T x2 = Xx * Xx + Xy * Xy + Xz * Xz;
-        fs += 8;
+        ++tl.cand;
         if ((float)x2 >= r2) continue;
         any = true;
-        fl += flops::per_image(L) - 8;
+        ++tl.img;
         T s[L + 1];
         seeds<L>(x2, alpha, aw, cw, pl, s);
         T Bt[D * D * D];
@@ -156,7 +155,7 @@ __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB,
                 for (int v = 0; v <= L - t - u; ++v) Rs[(t * D + u) * D + v] += Bt[(t * D + u) * D + v];
     }
     if (!any) return;
-    fl += flops::per_prim_quartet(LA, LB, LC, LD) - (31 + 45) - 3 * flops::herm_E(LC, LD);
+    ++tl.term;
     const T tp = T(kTwoPi52) * x.K * y.K * ip * iq / sqrt(x.p + y.p);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -318,7 +317,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_w(PlanDev pl, int 
 #pragma unroll
         for (int b = 0; b < NB; ++b) Dij[a * NB + b] = __ldg(Dp + (size_t)(aoI + a) * n + aoJ + b);
     const float tauf = (float)tau;
-    unsigned long long fl = 0, fs = 0, used = 0, slots = 0;
+    Tally tl;
+    unsigned used = 0, slots = 0;  // lane-terms processed and lane slots offered
     unsigned nq = 0;
     for (int kb = kbeg & ~31; kb < kend; kb += 32) {
         const int kt = kb + lane;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_w(PlanDev pl, int 
                 PrimE<LC, LD, T> kp;
                 PpiF kf;
                 load_prim<LC, LD, T>(pl, kpp, kp, kf);
-                fl += 3 * flops::herm_E(LC, LD);
+                ++tl.ketp;
                 const float Bk = __ldg(pl.ppB + kpp);
                 // bra primitives in descending order of their bound B: the
                 // first one whose B_i B_k is below the magnitude threshold ends
@@ -392,12 +392,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_w(PlanDev pl, int 
                     PrimE<LA, LB, T> bp;
                     PpiF bf;
                     load_prim<LA, LB, T>(pl, sb.pp0 + i, bp, bf);
-                    fs += flops::per_bra_prim(LA, LB);  // recomputed per lane: bookkeeping
-                    prim_term<LA, LB, LC, LD, T>(pl, bp, bf, kp, kf, V, fl, fs);
+                    ++tl.brap;  // recomputed per lane: bookkeeping
+                    prim_term<LA, LB, LC, LD, T>(pl, bp, bf, kp, kf, V, tl);
                     ++used;
                 }
             }
-            slots += (lane == 0) ? 32ull * sb.npp : 0ull;
+            slots += (lane == 0) ? 32u * sb.npp : 0u;
             // segmented sum over the lanes holding the same ket (contiguous)
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_w(PlanDev pl, int 
                 const SpiRec skh = pl.spi[okt];
                 const T w = T(sb.w) * T(skh.w) * ((same && okt == bra) ? T(0.5) : T(1));
                 digest<LA, LB, LC, LD, T>(pl, sb, skh, V, w, Dp, Dij, jb, X, Y);
-                fl += flops::per_quartet(LA, LB, LC, LD);
+                ++tl.quart;
             }
         }
     }
@@ -427,19 +427,228 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_w(PlanDev pl, int 
             const double v = warp_sum(jb[a * NB + b].value());
             if (lane == 0 && v != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, v);
         }
+    unsigned long long fl = tally_alg<LA, LB, LC, LD>(tl), fs = tally_screen<LA, LB, LC, LD>(tl), u64 = used, s64 = slots;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fl += __shfl_xor_sync(0xffffffffu, fl, o);
         fs += __shfl_xor_sync(0xffffffffu, fs, o);
-        used += __shfl_xor_sync(0xffffffffu, used, o);
-        slots += __shfl_xor_sync(0xffffffffu, slots, o);
+        u64 += __shfl_xor_sync(0xffffffffu, u64, o);
+        s64 += __shfl_xor_sync(0xffffffffu, s64, o);
     }
     if (lane == 0) {
         if (nq) atomicAdd(cnt, (unsigned long long)nq);
         if (fl) atomicAdd(cnt + 4, fl);
         if (fs) atomicAdd(cnt + 8, fs);
-        if (used) atomicAdd(cnt + 12, used);
-        if (slots) atomicAdd(cnt + 14, slots);
+        if (u64) atomicAdd(cnt + 12, u64);
+        if (s64) atomicAdd(cnt + 14, s64);
+    }
+}
+
+// Pair-queue tile kernel (third family for s and p class pairs): as the
+// lane-per-bra kernel, a warp holds 32 consecutive bras and walks the kets of
+// its chunk; but every (bra, ket) image pair that passes the quartet-level
+// bound goes into a per-warp queue in shared memory, and the queue is
+// evaluated 32 pairs at a time, one pair per lane, so lanes whose own bra
+// misses a ket do not idle while the others work.  The pairs of one batch
+// are ordered by ket, so the ket-side Coulomb term is summed over the lanes
+// of a ket by a segmented warp reduction; the bra-side term is added to the
+// bra's FP64 partial in shared memory; exchange as in the other kernels.
+template <int LA, int LB, int LC, int LD, typename T>
+__global__ void __launch_bounds__(kRealThreads) k_real_q(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
+                                                          double tau, const T *__restrict__ Dp, const T *__restrict__ dmax,
+                                                          double *__restrict__ X, double *__restrict__ Y,
+                                                          unsigned long long *__restrict__ cnt, int2 *__restrict__ big,
+                                                          unsigned *__restrict__ nbig, unsigned cap, unsigned *__restrict__ ovf)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD), NV = NA * NB * NC * ND;
+    constexpr int L = LA + LB + LC + LD;
+    constexpr int NW = kRealThreads / 32;
+    __shared__ int qall[NW][64];
+    __shared__ double jball[NW][32 * NA * NB];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int *qb = qall[wid];
+    double *jbs = jball[wid];
+    const int wbra0 = b0 + blockIdx.x * kRealThreads + 32 * wid;  // the warp's first bra
+    const int bra = wbra0 + lane;
+    int kbeg = k0 + blockIdx.y * kchunk;
+    const int kend = min(k1, kbeg + kchunk);
+    if (same) kbeg = max(kbeg, wbra0);
+    if (kbeg >= kend || wbra0 >= b1) return;  // whole warp; no block-wide barrier below
+    const bool act = bra < b1;
+    const SpiRec sb = pl.spi[act ? bra : b0];
+    const int n = pl.nbf, nsh = pl.nshell;
+#pragma unroll
+    for (int q = 0; q < NA * NB; ++q) jbs[lane * NA * NB + q] = 0.0;
+    __syncwarp();
+    const float tauf = (float)tau;
+    unsigned nq = 0, qn = 0, qd = 0;
+    Tally tl;
+    // evaluate `count` queued pairs, one per lane
+    auto process = [&](unsigned count) {
+        const bool on = lane < count;
+        int o = 0, kt = 0;
+        if (on) {
+            const int item = qb[(qd + lane) & 63];
+            o = item & 31;
+            kt = item >> 5;
+        }
+        T V[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) V[q] = T(0);
+        SpiRec sbo{}, sk{};
+        if (on) {
+            sbo = pl.spi[wbra0 + o];
+            sk = pl.spi[kt];
+            quartet_block<LA, LB, LC, LD, T>(pl, sbo, sk, V, tl);
+            ++tl.quart;
+            ++nq;
+        }
+        const T w = on ? T(sbo.w) * T(sk.w) * ((same && kt == wbra0 + o) ? T(0.5) : T(1)) : T(0);
+        const int aoI = pl.shells[on ? sbo.I : sb.I].ao, aoJ = pl.shells[on ? sbo.J : sb.J].ao;
+        const int aoK = pl.shells[on ? sk.I : sb.I].ao, aoL = pl.shells[on ? sk.J : sb.J].ao;
+        auto Dd = [&](int r, int c) { return __ldg(Dp + (size_t)r * n + c); };
+        // bra-side Coulomb: the bra's FP64 partial in shared memory
+        if (on) {
+#pragma unroll
+            for (int ab = 0; ab < NA * NB; ++ab) {
+                T s2 = T(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) s2 += V[ab * NC * ND + c * ND + d] * Dd(aoK + c, aoL + d);
+                if (s2 != T(0)) atomicAdd(jbs + o * NA * NB + ab, to_f64(T(2) * w * s2));
+            }
+        }
+        // ket-side Coulomb: segmented sum over the lanes of one ket (the batch is ordered by ket)
+        const int key = on ? kt : -1 - lane;
+#pragma unroll
+        for (int cd = 0; cd < NC * ND; ++cd) {
+            T s2 = T(0);
+            if (on) {
+                T Dij[NA * NB];
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) Dij[a * NB + b] = Dd(aoI + a, aoJ + b);
+#pragma unroll
+                for (int ab = 0; ab < NA * NB; ++ab) s2 += V[ab * NC * ND + cd] * Dij[ab];
+                s2 *= T(2) * w;
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
+                const T t2 = __shfl_down_sync(0xffffffffu, s2, off);
+                if (lane + off < 32 && ok2 == key) s2 += t2;
+            }
+            const int prevk = __shfl_up_sync(0xffffffffu, key, 1);
+            if (on && (lane == 0 || prevk != key) && s2 != T(0))
+                atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, to_f64(s2));
+        }
+        // exchange: the four index assignments of the orbit (the other four are transposes)
+        if (on) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    T s2 = T(0);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) s2 += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoJ + b, aoK + c);
+                    atomicAdd(Y + (size_t)(aoI + a) * n + aoL + d, to_f64(w * s2));
+                }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    T s2 = T(0);
+#pragma unroll
+                    for (int a = 0; a < NA; ++a)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) s2 += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoI + a, aoK + c);
+                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoL + d, to_f64(w * s2));
+                }
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    T s2 = T(0);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) s2 += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoJ + b, aoL + d);
+                    atomicAdd(Y + (size_t)(aoI + a) * n + aoK + c, to_f64(w * s2));
+                }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    T s2 = T(0);
+#pragma unroll
+                    for (int a = 0; a < NA; ++a)
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) s2 += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoI + a, aoL + d);
+                    atomicAdd(Y + (size_t)(aoJ + b) * n + aoK + c, to_f64(w * s2));
+                }
+        }
+        qd += count;
+        __syncwarp();
+    };
+    for (int kt = kbeg; kt < kend; ++kt) {
+        // one bound per block of 32 kets for the whole warp first
+        if (kt == kbeg || (kt & 31) == 0) {
+            if (!__any_sync(0xffffffffu, act && block_reaches<L>(pl, sb, kt >> 5))) {
+                kt = min(kend, ((kt >> 5) + 1) << 5) - 1;
+                continue;
+            }
+        }
+        const SpiRec sk = pl.spi[kt];
+        bool valid = act && (!same || kt >= bra) && quartet_reaches<L>(pl, sb, sk);
+        if (sizeof(T) == 4 && valid && mode) {
+            const float dm = quartet_dmax(reinterpret_cast<const float *>(dmax), nsh, sb, sk);
+            const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
+            const float ipq = 1.0f / sb.pmin + 1.0f / sk.pmin;
+            if (est >= tauf || ipq > 0.7225f * (ipq + pl.inv_omega2f)) {
+                const unsigned slot = atomicAdd(nbig, 1u);
+                if (slot < cap) {
+                    big[slot] = make_int2(bra, kt);
+                    valid = false;
+                } else {
+                    atomicAdd(ovf, 1u);
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (!m) continue;
+        if (valid) qb[(qn + __popc(m & ((1u << lane) - 1u))) & 63] = (kt << 5) | lane;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn - qd >= 32) process(32);
+    }
+    while (qn > qd) process(min(32u, qn - qd));
+    // the bra-side Coulomb partials of the warp's bras
+    if (act) {
+        const int aoI = pl.shells[sb.I].ao, aoJ = pl.shells[sb.J].ao;
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const double v = jbs[lane * NA * NB + a * NB + b];
+                if (v != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, v);
+            }
+    }
+    unsigned long long fl = tally_alg<LA, LB, LC, LD>(tl), fs = tally_screen<LA, LB, LC, LD>(tl);
+    unsigned tot = nq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        fl += __shfl_xor_sync(0xffffffffu, fl, o);
+        fs += __shfl_xor_sync(0xffffffffu, fs, o);
+    }
+    if (lane == 0) {
+        if (tot) atomicAdd(cnt, (unsigned long long)tot);
+        if (fl) atomicAdd(cnt + 4, fl);
+        if (fs) atomicAdd(cnt + 8, fs);
     }
 }
 
@@ -462,7 +671,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_list_w(PlanDev pl,
     int *qbuf = qall[threadIdx.x >> 5];
     const unsigned total = min(*nbig, cap);
     const int n = pl.nbf;
-    unsigned long long fl = 0, fs = 0, used = 0, slots = 0;
+    Tally tl;
+    unsigned used = 0, slots = 0;
     unsigned done = 0;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
     for (unsigned q = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); q < total; q += nwarps) {
@@ -482,8 +692,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_list_w(PlanDev pl,
                 PpiF bf, kf;
                 load_prim<LA, LB, double>(pl, sb.pp0 + i, bp, bf);
                 load_prim<LC, LD, double>(pl, sk.pp0 + j, kp, kf);
-                fl += flops::per_bra_prim(LA, LB) + 3 * flops::herm_E(LC, LD);
-                prim_term<LA, LB, LC, LD, double>(pl, bp, bf, kp, kf, V, fl, fs);
+                ++tl.brap;
+                ++tl.ketp;
+                prim_term<LA, LB, LC, LD, double>(pl, bp, bf, kp, kf, V, tl);
                 ++used;
             }
             if (lane == 0) slots += 32;
@@ -497,7 +708,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_list_w(PlanDev pl,
                 const int i = t / sk.npp, j = t - i * sk.npp;
                 pass = __ldg(pl.ppB + sb.pp0 + i) * __ldg(pl.ppB + sk.pp0 + j) >= pl.mag_thr &&
                        prim_reaches<L>(pl, pl.ppf[sb.pp0 + i], pl.ppf[sk.pp0 + j]);
-                fs += flops::per_prim_screen() + 31 + 30;
+                ++tl.screen;
             }
             const unsigned m = __ballot_sync(0xffffffffu, pass);
             if (pass) qbuf[(qn + __popc(m & ((1u << lane) - 1u))) & 63] = t;
@@ -519,6 +730,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_list_w(PlanDev pl,
                 for (int b = 0; b < NB; ++b) Dij[a * NB + b] = __ldg(Dp + (size_t)(aoI + a) * n + aoJ + b);
             const double w = double(sb.w) * double(sk.w) * ((same && pr.x == pr.y) ? 0.5 : 1.0);
             digest<LA, LB, LC, LD, double>(pl, sb, sk, V, w, Dp, Dij, jb, X, Y);
+            ++tl.quart;
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
@@ -526,23 +738,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_list_w(PlanDev pl,
                     const double v = jb[a * NB + b].value();
                     if (v != 0.0) atomicAdd(X + (size_t)(aoI + a) * n + aoJ + b, v);
                 }
-            fl += flops::per_quartet(LA, LB, LC, LD);
         }
         __syncwarp();
     }
+    unsigned long long fl = tally_alg<LA, LB, LC, LD>(tl), fs = tally_screen<LA, LB, LC, LD>(tl), u64 = used, s64 = slots;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fl += __shfl_xor_sync(0xffffffffu, fl, o);
         fs += __shfl_xor_sync(0xffffffffu, fs, o);
-        used += __shfl_xor_sync(0xffffffffu, used, o);
-        slots += __shfl_xor_sync(0xffffffffu, slots, o);
+        u64 += __shfl_xor_sync(0xffffffffu, u64, o);
+        s64 += __shfl_xor_sync(0xffffffffu, s64, o);
     }
     if (lane == 0) {
         if (done) atomicAdd(cnt, (unsigned long long)done);
         if (fl) atomicAdd(cnt + 4, fl);
         if (fs) atomicAdd(cnt + 8, fs);
-        if (used) atomicAdd(cnt + 12, used);
-        if (slots) atomicAdd(cnt + 14, slots);
+        if (u64) atomicAdd(cnt + 12, u64);
+        if (s64) atomicAdd(cnt + 14, s64);
     }
 }
 

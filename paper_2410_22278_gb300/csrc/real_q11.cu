@@ -13,6 +13,18 @@ void launch_real_q11(const RealLaunch &a)
                                                                                   a.cnt64);
         return;
     }
+    if (a.variant == 2) {
+        dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+        if (a.fp32)
+            k_real_q<1, 0, 1, 0, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
+                                                                                 a.mode, a.tau, a.Dpf, a.dmaxf, a.X, a.Y, a.cnt, a.big,
+                                                                                 a.nbig, a.cap, a.ovf);
+        else
+            k_real_q<1, 0, 1, 0, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
+                                                                                  a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big,
+                                                                                  a.nbig, a.cap, a.ovf);
+        return;
+    }
     if (a.variant == 0) {
         dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
         if (a.fp32)

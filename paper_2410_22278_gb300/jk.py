@@ -222,16 +222,16 @@ class Plan:
                                    stream or None), "jk_build_host")
 
     PHASES = ["prologue", "real_space", "recip_sfac", "recip_j", "recip_k", "epilogue", "total", "tensor_gemm", "tensor_slice",
-              "real_fp64_list"]
+              "real_fp64_list", "real_tiles"]
 
     def build_times(self):
         """{phase: (ms, launches)} of the most recent build (device events),
         plus "mma_flops": BF16 MMA flops issued by the tensor-core GEMMs."""
-        ms = (ctypes.c_double * 11)()
-        nl = (ctypes.c_int * 11)()
-        _check(lib().jk_build_times(self._h, ms, nl, 11), "jk_build_times")
+        ms = (ctypes.c_double * 12)()
+        nl = (ctypes.c_int * 12)()
+        _check(lib().jk_build_times(self._h, ms, nl, 12), "jk_build_times")
         out = {p: (ms[i], nl[i]) for i, p in enumerate(self.PHASES)}
-        out["mma_flops"] = (ms[10], 0)
+        out["mma_flops"] = (ms[11], 0)
         return out
 
     def autotune(self, D_ptr: int, stream: int = 0, cache_path: str = None):

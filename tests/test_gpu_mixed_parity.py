@@ -187,17 +187,18 @@ def test_two_threads_one_plan(jk):
         plan.close()
 
 
-@pytest.mark.parametrize("family", [0, 1])
+@pytest.mark.parametrize("family", [0, 1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_both_kernel_families_match_oracle(jk, family, precision):
-    """The s and p class pairs have two real-space kernel families (lane per
-    bra, warp per bra); either, forced through jk_plan_set_schedule for every
-    such class pair, matches the oracle on a skewed s/p/d cell."""
+def test_every_kernel_family_matches_oracle(jk, family, precision):
+    """The s and p class pairs have three real-space kernel families (lane
+    per bra, warp per bra, pair queue); each, forced through
+    jk_plan_set_schedule for every such class pair, matches the oracle on a
+    skewed s/p/d cell."""
     cell = sc.small_random_cell(3, natom=2, lmax=2)
     D, Jo, Ko, _ = oracle_jk(cell)
     plan = jk.plan_from_cell(cell, precision=precision)
     classes = [(a, b) for a in range(6) for b in range(a, 6)]
-    plan.set_schedule([(family if (a <= 2 and b <= 2) else 0, 512 if (family and a <= 2 and b <= 2) else 16)
+    plan.set_schedule([(family if (a <= 2 and b <= 2) else 0, 512 if (family == 1 and a <= 2 and b <= 2) else 16)
                        for a, b in classes])
     dev = torch.device("cuda:0")
     Dt = torch.from_numpy(D).to(dev)
@@ -211,3 +212,38 @@ def test_both_kernel_families_match_oracle(jk, family, precision):
     assert np.abs(K.cpu().numpy() - Ko).max() < tol
     with pytest.raises(jk.JkError):
         jk.plan_from_cell(cell).set_schedule([(1, 16)] * 21)  # no warp kernels for d classes
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reciprocal_cache(jk, precision):
+    """jk_plan_cache: the build that fills the cache and the builds that read
+    it give the uncached result (the cached data are D-independent), also
+    for a different density; 0 releases the cache."""
+    cell = sc.small_random_cell(4, natom=3, lmax=1)
+    dev = torch.device("cuda:0")
+    D1 = torch.from_numpy(O.density(cell)).to(dev)
+    D2 = torch.from_numpy(O.density(cell) + sc.density_perturbation(99, cell.nbf)).to(dev)
+
+    def build(plan, D):
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        plan.build(D.data_ptr(), J.data_ptr(), K.data_ptr(), 0)
+        torch.cuda.synchronize()
+        return J.cpu().numpy(), K.cpu().numpy()
+
+    plain = jk.plan_from_cell(cell, precision=precision)
+    ref1, ref2 = build(plain, D1), build(plain, D2)
+    plain.close()
+    plan = jk.plan_from_cell(cell, precision=precision)
+    nbytes = plan.cache(1 << 30)
+    assert nbytes > 0 and plan.info()["device_bytes"] >= nbytes
+    for D, ref in [(D1, ref1), (D1, ref1), (D2, ref2)]:
+        J, K = build(plan, D)
+        assert np.abs(J - ref[0]).max() < 1e-12 and np.abs(K - ref[1]).max() < 1e-12
+    assert plan.cache(0) == 0
+    with pytest.raises(jk.JkError) as e:
+        plan.cache(16)  # far too small: refused, the plan works as before
+    assert e.value.status == jk.JK_ERR_OOM
+    J, K = build(plan, D2)
+    assert np.abs(J - ref2[0]).max() < 1e-12
+    plan.close()
