@@ -84,6 +84,11 @@ WORKLOADS = {
     # same density and basis, 16 molecules: the small case for ncu captures
     "water16": ("water16: 16 H2O, a=7.82 A, 208 bf, omega=0.4, thresholds 1e-14",
                 lambda sc: sc.water_cell(16, 12.42 / 4 ** (1.0 / 3.0), omega=0.4, n_occ=64, geo_purpose=3)),
+    # the large single cell: 6x6x6 diamond, 1728 atoms, s(6) s(4) p(1), 8640 bf
+    "large1728": ("large1728: diamond 6x6x6, 1728 atoms, a=21.40 A, 8640 bf, omega=0.4, Schwarz 1e-11",
+                  lambda sc: sc.config(5)),
+    # the diamond supercell: 3x3x3, 216 atoms, s(6) s(3) p(1) d(1), 2376 bf
+    "diamond216": ("diamond216: diamond 3x3x3, 216 atoms, a=10.70 A, 2376 bf, omega=0.5", lambda sc: sc.config(3)),
 }
 
 
@@ -262,6 +267,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="water64", choices=sorted(WORKLOADS))
     ap.add_argument("--profile", action="store_true", help="mixed builds only (for ncu captures)")
+    ap.add_argument("--coulomb-only", action="store_true", help="with --profile: time J-only builds (K = NULL)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default real-space schedule")
     ap.add_argument("--serving", action="store_true", help="run the serving stream instead of the single-cell build")
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--max-atoms", type=int, default=64)
@@ -311,10 +318,10 @@ def main():
     K = torch.empty_like(D)
 
     def build(p):
-        p.build(D.data_ptr(), J.data_ptr(), K.data_ptr(), st)
+        p.build(D.data_ptr(), J.data_ptr(), 0 if (args.profile and args.coulomb_only) else K.data_ptr(), st)
 
     # tile shapes of the real-space kernels chosen by the library's autotuner (outside the timed region)
-    tiles = plan.autotune(D.data_ptr(), st, args.autotune_cache)
+    tiles = None if args.no_autotune else plan.autotune(D.data_ptr(), st, args.autotune_cache)
     for _ in range(args.warmup):
         build(plan)
     stream.synchronize()
@@ -365,7 +372,8 @@ def main():
     Jm, Km = J.cpu().numpy(), K.cpu().numpy()
     ej, ek = plan.energy(D.data_ptr(), J.data_ptr(), K.data_ptr(), st)
     if args.profile:
-        print(json.dumps({"profile": args.workload, "mixed_switch": args.mixed_switch, "ms_per_step": ms_per_step, "phases_ms": {k2: v for k2, v in phases.items()},
+        print(json.dumps({"profile": args.workload, "coulomb_only": args.coulomb_only, "nbf": n, "plan": info,
+                          "mixed_switch": args.mixed_switch, "ms_per_step": ms_per_step, "phases_ms": {k2: v for k2, v in phases.items()},
                           "counts": counts, "counters": plan.counters(), "schedule": tiles,
                           "phases_ms_without_cache": phases_nocache, "cache_bytes": cache_bytes}))
         return 0
@@ -390,6 +398,27 @@ def main():
         return {"max_abs_dJ": dj, "max_abs_dK": dk, "rows_compared": rows} if rows else None
 
     mixed_vs_oracle = vs_oracle(Jm, Km)
+
+    # ---- Coulomb-only builds of the same plan (J alone, K = NULL): the
+    # Hermite J-engine path
+    def build_j(p):
+        p.build(D.data_ptr(), J.data_ptr(), 0, st)
+
+    build_j(plan)
+    stream.synchronize()
+    ej_only = []
+    for _ in range(max(2, args.steps // 2)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        build_j(plan)
+        b.record(stream)
+        stream.synchronize()
+        ej_only.append(a.elapsed_time(b))
+    jonly_phases = {k2: v[0] for k2, v in plan.build_times().items() if k2 != "mma_flops"}
+    Jonly = J.cpu().numpy()
+    coulomb_only = {"ms_per_build": statistics.median(ej_only), "builds_per_s": 1e3 / statistics.median(ej_only),
+                    "max_abs_dJ_vs_JK_build": float(np.abs(Jonly - Jm).max()), "phases_ms": jonly_phases,
+                    "path": "Hermite J-engine (K = NULL)"}
 
     # ---- FP64 GPU form on the same GPU
     build(plan64)
@@ -476,6 +505,7 @@ def main():
         "clocks": cl,
         "e2e": {"value": 1.0 / e2e_s, "unit": "builds/s", "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8},
         "serving": serving,
+        "coulomb_only": coulomb_only,
     }
     if not args.no_cpu_baseline and world == 1:
         from oracle import oracle as O

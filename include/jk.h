@@ -108,8 +108,8 @@ typedef struct {
 
 /* Build the plan for one cell (Sections 3.1, 3.3, 3.4): normalise the
  * shells, build the local-pair lists over lattice images with the pair
- * cut-offs of Eqs. 434 and 450 (minimum-image offsets, Eq.
- * lattice_image_min_norm), Schwarz estimates (Eq. 445) and quartet classes,
+ * cut-offs of Eqs. pbc_eri_pair_cutoff_implementation and pbc_eri_cauchy_schwarz_cutoff_implementation (minimum-image offsets, Eq.
+ * lattice_image_min_norm), Schwarz estimates (Eq. pbc_eri_cauchy_schwarz_cutoff_definition) and quartet classes,
  * the reciprocal vector list, and upload everything to `device`.
  * omega <= 0 selects Eq. omega_implementation with w = 10.
  * cut == NULL means all defaults.  On success *out owns device memory until
@@ -192,7 +192,10 @@ int jk_energy(const jk_plan *plan, const double *D, const double *J, const doubl
  * naming the limit (use jk_energy there).
  * First call on a device: looks up the array's device address once
  * (cudaGetSymbolAddress with the plan's device current); make that first
- * call before any stream capture begins.
+ * call before any stream capture begins.  The address is kept for the life
+ * of the process, so the device's primary context must outlive the
+ * library's use of it: after a cudaDeviceReset (or another replacement of
+ * the primary context) do not call this entry point again.
  * Concurrency: all calls on one device share the array, so two calls whose
  * work overlaps on the GPU (different streams or host threads) race and may
  * return wrong sums; serialise them.

@@ -11,7 +11,7 @@
  *   - ordered shell pairs, no permutational symmetry, no quartet screening;
  *   - Ewald sums truncated far past the GPU's thresholds (delta 1e-18 plus a
  *     distance margin), so that the only truncation it shares with the GPU
- *     is the pair list, whose definition (Eqs. 434/450) defines the object;
+ *     is the pair list, whose definition (Eqs. pbc_eri_pair_cutoff_implementation / pbc_eri_cauchy_schwarz_cutoff_implementation) defines the object;
  *   - the real-space (erfc) part follows Eq. pbc_eri_general_final term by
  *     term: McMurchie-Davidson E coefficients (Eqs. E_recursion_*), the
  *     attenuated Boys seeds of Eq. boys_function_split and the R recursion
@@ -85,7 +85,7 @@ typedef struct {
     const double *exps, *coefs, *centers; /* raw coefficients */
     double lat[9];                        /* rows a, b, c */
     double omega;                         /* 0: bare Coulomb, inf: reciprocal only */
-    double pair_R, pair_cs;               /* pair-list thresholds (Eqs. 434, 450) */
+    double pair_R, pair_cs;               /* pair-list thresholds (Eqs. pbc_eri_pair_cutoff_implementation, pbc_eri_cauchy_schwarz_cutoff_implementation) */
     double delta;                         /* Ewald truncation used by the oracle */
     double margin;                        /* extra real-space radius, bohr */
 } orc_basis;

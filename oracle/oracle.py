@@ -145,7 +145,7 @@ def norm_coefs(l, exps, coefs) -> np.ndarray:
 
 def pair_counts(cell):
     """(ordered shell pairs, ordered primitive pairs, ordered local pairs)
-    after the pair cut-offs of Eqs. 434 and 450 (Section 3.1)."""
+    after the pair cut-offs of Eqs. pbc_eri_pair_cutoff_implementation and pbc_eri_cauchy_schwarz_cutoff_implementation (Section 3.1)."""
     b = Basis(cell)
     c = (ctypes.c_long * 3)()
     lib().orc_pair_counts(b.ref(), c)

@@ -18,6 +18,7 @@
 #include <map>
 #include <string>
 
+#include "jeng.cuh"
 #include "kernels.cuh"
 #include "launch.h"
 #include "plan.h"
@@ -170,6 +171,34 @@ void launch_gauss_table(const Plan *P, int g0, int gcur, double *tab, cudaStream
 }
 
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+// Hermite densities (back = false) or the Hermite-to-Cartesian step (back =
+// true) of the J-engine for the images of class cls (l_I >= l_J)
+template <int LA, int LB>
+static void hermite_go(bool back, const PlanDev &pl, int b0, int b1, const Workspace &w, const double *Dp, bool f32, double *X,
+                       cudaStream_t st)
+{
+    if (b1 <= b0) return;
+    const unsigned g = (unsigned)((b1 - b0 + 127) / 128);
+    if (back)
+        k_hermite_back<LA, LB><<<g, 128, 0, st>>>(pl, b0, b1, w.hs, w.JH, X);
+    else
+        k_hermite_density<LA, LB><<<g, 128, 0, st>>>(pl, b0, b1, Dp, w.hs, w.DhD, f32 ? w.DhF : nullptr);
+}
+
+static void launch_hermite(int cls, bool back, const PlanDev &pl, int b0, int b1, const Workspace &w, const double *Dp, bool f32,
+                           double *X, cudaStream_t st)
+{
+    switch (cls) {
+    case 0: hermite_go<0, 0>(back, pl, b0, b1, w, Dp, f32, X, st); break;
+    case 1: hermite_go<1, 0>(back, pl, b0, b1, w, Dp, f32, X, st); break;
+    case 2: hermite_go<1, 1>(back, pl, b0, b1, w, Dp, f32, X, st); break;
+    case 3: hermite_go<2, 0>(back, pl, b0, b1, w, Dp, f32, X, st); break;
+    case 4: hermite_go<2, 1>(back, pl, b0, b1, w, Dp, f32, X, st); break;
+    case 5: hermite_go<2, 2>(back, pl, b0, b1, w, Dp, f32, X, st); break;
+    default: break;
+    }
+}
 
 static int cuda_check(const char *what)
 {
@@ -327,6 +356,20 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
     if (mixed && K && (rc = ozaki_begin(P, st))) return rc;
     tm.stop(0, ev, mixed ? (K ? 8 : 4) : 1);
 
+    // Coulomb-only build: the J-engine (Hermite densities in, Hermite J out)
+    // (only the classes with a d shell, l_I = 2, take part: kJengClass)
+    constexpr int kJengClass = 3;
+    bool have_d = false;
+    for (int c = kJengClass; c < JK_NCLASS_MAX; ++c) have_d = have_d || P->classes[c].b1 > P->classes[c].b0;
+    const bool jeng = J && !K && have_d;
+    if (jeng) {
+        const int eh = tm.start(0);
+        cudaMemsetAsync(w.JH, 0, std::max<size_t>(1, P->ppi.size()) * w.hs * sizeof(double), st);
+        for (int c = kJengClass; c < JK_NCLASS_MAX; ++c)
+            launch_hermite(c, false, pl, P->classes[c].b0, P->classes[c].b1, w, w.Dp, mixed, nullptr, st);
+        tm.stop(0, eh, JK_NCLASS_MAX - kJengClass + 1);
+    }
+
     // ---- real space (the phases run one after another on the caller's
     // stream: run on streams of their own they gained nothing on the water
     // box -- the tile kernels fill every SM, and the tensor-core GEMMs, which
@@ -352,9 +395,48 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             a.Dpf = w.Dpf;
             a.dmaxf = w.dmaxf;
             a.X = w.X;
-            a.Y = w.Y;
+            a.Y = K ? w.Y : nullptr;
             a.st = st;
-            if (!mixed) {
+            a.DhD = w.DhD;
+            a.DhF = w.DhF;
+            a.JH = w.JH;
+            a.hs = w.hs;
+            // Coulomb-only builds take the J-engine for class pairs with a d
+            // shell on both sides, where the Hermite contraction is smaller
+            // than the Cartesian block (measured: for s and p classes the
+            // Cartesian kernels with the exchange digestion skipped are
+            // faster); its tiles are lane-per-bra: kets per tile as tuned for
+            // that family, else 32
+            const bool use_jeng = jeng && cb >= kJengClass && ck >= kJengClass;
+            if (use_jeng && a.variant != 0) a.kchunk = 32;
+            if (use_jeng && !mixed) {
+                a.mode = 0;
+                a.fp32 = false;
+                a.cnt = w.cnt;
+                const int et = tm.start(10);
+                launch_jeng(cb, ck, a);
+                tm.stop(10, et, 1);
+                nreal += 1;
+            } else if (use_jeng) {
+                cudaMemsetAsync(w.nbig, 0, sizeof(unsigned), st);
+                a.mode = 2;
+                a.fp32 = true;
+                a.cnt = w.cnt + 1;
+                a.big = w.big;
+                a.nbig = w.nbig;
+                a.ovf = w.nbig + 1;
+                a.cap = w.cap;
+                const int et = tm.start(10);
+                launch_jeng(cb, ck, a);
+                tm.stop(10, et, 1);
+                // the listed large quartets: the Cartesian FP64 pass, Coulomb only
+                a.list_pass = true;
+                a.cnt64 = w.cnt;
+                const int el = tm.start(9);
+                launch_real(cb, ck, a);
+                tm.stop(9, el, 1);
+                nreal += 2;
+            } else if (!mixed) {
                 a.mode = 0;
                 a.fp32 = false;
                 a.cnt = w.cnt;
@@ -385,6 +467,12 @@ int run_build(Plan *P, const double *D, double *J, double *K, cudaStream_t st)
             }
             if ((rc = cuda_check("real-space kernel"))) return rc;
         }
+    if (jeng) {
+        // Hermite J of every primitive pair back to Cartesian, into X
+        for (int c = kJengClass; c < JK_NCLASS_MAX; ++c)
+            launch_hermite(c, true, pl, P->classes[c].b0, P->classes[c].b1, w, nullptr, false, w.X, st);
+        nreal += JK_NCLASS_MAX - kJengClass;
+    }
     tm.stop(1, ev, nreal);
 
     // ---- reciprocal space

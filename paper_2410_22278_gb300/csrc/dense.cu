@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_slab_axpy(const double *__restrict__ M,
 
 int slab_dot_splits(long long n2, int m2)
 {
-    // about eight blocks per SM in total, at least 4096 elements per block
+    // about eight blocks per SM in total (a chunk of one G vector has only two
+    // slabs), at least 4096 elements per block
     const long long want = std::max(1LL, (152LL * 8 + m2 - 1) / std::max(1, m2));
     return (int)std::max(1LL, std::min({want, (n2 + 4095) / 4096, (long long)kSlabSplitsMax}));
 }

@@ -20,7 +20,7 @@ struct LowRankWs {
 
 // rho[b] = sum_i M[b][i] x[i] for b < m2 (M is [m2][n2]); part holds
 // m2 * kSlabSplitsMax partial sums.
-constexpr int kSlabSplitsMax = 64;
+constexpr int kSlabSplitsMax = 1024;
 void slab_gemv_t(const double *M, long long n2, int m2, const double *x, double *part, double *rho, cudaStream_t st);
 // y[i] += alpha sum_b M[b][i] rho[b].
 void slab_gemv_n(const double *M, long long n2, int m2, const double *rho, double alpha, double *y, cudaStream_t st);

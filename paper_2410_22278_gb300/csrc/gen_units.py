@@ -10,6 +10,7 @@ CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
 # kernels (their Cartesian blocks are too large for a warp-wide segmented
 # reduction in registers).
 UNIT_W = """// Real-space quartet kernels for bra class {lab} and ket class {lcd} (generated by gen_units.py).
+#include "jeng.cuh"
 #include "launch.h"
 #include "real2.cuh"
 
@@ -59,10 +60,26 @@ void launch_real_q{cb}{ck}(const RealLaunch &a)
                                                                                   a.nbig, a.cap, a.ovf);
 }}
 
+void launch_jeng_q{cb}{ck}(const RealLaunch &a)
+{{
+    const int nb = a.b1 - a.b0, nk = a.k1 - a.k0;
+    if (nb <= 0 || nk <= 0) return;
+    dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+    if (a.fp32)
+        k_jeng<{la}, {lb}, {lc}, {ld}, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                           a.tau, a.dmaxf, a.DhF, a.hs, a.X, a.JH, a.cnt, a.big, a.nbig,
+                                                                           a.cap, a.ovf);
+    else
+        k_jeng<{la}, {lb}, {lc}, {ld}, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                            a.tau, a.dmax, a.DhD, a.hs, a.X, a.JH, a.cnt, a.big, a.nbig,
+                                                                            a.cap, a.ovf);
+}}
+
 }}  // namespace jk
 """
 
 UNIT = """// Real-space quartet kernels for bra class {lab} and ket class {lcd} (generated by gen_units.py).
+#include "jeng.cuh"
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -85,6 +102,21 @@ void launch_real_q{cb}{ck}(const RealLaunch &a)
                                                                         a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big, a.nbig, a.cap, a.ovf);
 }}
 
+void launch_jeng_q{cb}{ck}(const RealLaunch &a)
+{{
+    const int nb = a.b1 - a.b0, nk = a.k1 - a.k0;
+    if (nb <= 0 || nk <= 0) return;
+    dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+    if (a.fp32)
+        k_jeng<{la}, {lb}, {lc}, {ld}, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                           a.tau, a.dmaxf, a.DhF, a.hs, a.X, a.JH, a.cnt, a.big, a.nbig,
+                                                                           a.cap, a.ovf);
+    else
+        k_jeng<{la}, {lb}, {lc}, {ld}, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                            a.tau, a.dmax, a.DhD, a.hs, a.X, a.JH, a.cnt, a.big, a.nbig,
+                                                                            a.cap, a.ovf);
+}}
+
 }}  // namespace jk
 """
 
@@ -103,11 +135,17 @@ def main():
         f.write("namespace jk {\n")
         for cb, ck in decls:
             f.write("void launch_real_q%d%d(const RealLaunch &a);\n" % (cb, ck))
+            f.write("void launch_jeng_q%d%d(const RealLaunch &a);\n" % (cb, ck))
         f.write("\n// class pairs of s and p shells have the warp kernels of real2.cuh as a second family\n")
         f.write("inline bool real_has_warp_kernel(int cb, int ck) { return cb <= 2 && ck <= 2; }\n")
         f.write("\ninline void launch_real(int cb, int ck, const RealLaunch &a)\n{\n    switch (cb * 8 + ck) {\n")
         for cb, ck in decls:
             f.write("    case %d: launch_real_q%d%d(a); break;\n" % (cb * 8 + ck, cb, ck))
+        f.write("    default: break;\n    }\n}\n\n")
+        f.write("// Coulomb-only builds: the J-engine kernel of a class pair (jeng.cuh)\n")
+        f.write("inline void launch_jeng(int cb, int ck, const RealLaunch &a)\n{\n    switch (cb * 8 + ck) {\n")
+        for cb, ck in decls:
+            f.write("    case %d: launch_jeng_q%d%d(a); break;\n" % (cb * 8 + ck, cb, ck))
         f.write("    default: break;\n    }\n}\n\n}  // namespace jk\n")
 
 

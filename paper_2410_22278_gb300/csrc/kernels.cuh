@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
             if ((threadIdx.x & 31) == 0 && s != T(0)) atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, to_f64(s));
         }
         // exchange: the four index assignments of the orbit (the other four are transposes)
-        if (valid) {
+        if (valid && Y) {
 #pragma unroll DUNR
             for (int a = 0; a < NA; ++a)
 #pragma unroll DUNR
@@ -636,6 +636,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real_list(PlanDev pl, const in
                     for (int b = 0; b < NB; ++b) s += V[((a * NB + b) * NC + c) * ND + d] * Dd(aoI + a, aoJ + b);
                 atomicAdd(X + (size_t)(aoK + c) * n + aoL + d, 2.0 * w * s);
             }
+        if (!Y) continue;  // a Coulomb-only build
 #pragma unroll DUNR
         for (int a = 0; a < NA; ++a)
 #pragma unroll DUNR

@@ -22,6 +22,12 @@ struct RealLaunch {
     bool list_pass;      // launch k_real_list over the list instead of the tile kernel
     int variant;         // 0 lane-per-bra tile kernel; for s and p class pairs also 1 warp, 2 pair-queue kernel (autotuned)
     unsigned long long *cnt64;
+    // Coulomb-only builds (J-engine): Hermite densities of the primitive
+    // pairs (stride hs) and their Hermite J accumulators
+    const double *DhD;
+    const float *DhF;
+    double *JH;
+    int hs;
     cudaStream_t st;
 };
 

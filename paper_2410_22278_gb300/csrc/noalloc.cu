@@ -16,7 +16,10 @@
 //
 // First call on a device: the array's device address is looked up once,
 // with cudaGetSymbolAddress on that device; make that first call before any
-// stream capture begins.
+// stream capture begins.  The address is kept for the life of the process:
+// it assumes the device's primary context outlives the library's use of it
+// (a cudaDeviceReset, or any other replacement of the primary context,
+// invalidates it; such a program must not call this entry point again).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     extern __shared__ uint8_t tc_dsm[];
     __shared__ __align__(8) uint64_t full[TC_ST], empty[TC_ST], acc_full[2], acc_empty[2];
+    __shared__ __align__(16) int cex_s[TC_EPI_WARPS][64];  // column exponents of the current batch, per epilogue warp
     __shared__ uint32_t tmem_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = tc::smem_u32(tc_dsm);
@@ -328,7 +329,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool fresh = true;
         for (int b = b0; b < b1 && ok; ++b) {
             const int rex = g.Aex[(size_t)(g.a_exb ? b : 0) * g.a_exb + r];
-            const int4 *cex4 = reinterpret_cast<const int4 *>(g.Bex + (size_t)(g.b_exb ? b : 0) * g.b_exb + col0 + 64 * half);
+            // the warp's 64 column exponents of this batch, staged once in
+            // shared memory (read back as broadcasts for every slice product)
+            {
+                const int *cex = g.Bex + (size_t)(g.b_exb ? b : 0) * g.b_exb + col0 + 64 * half;
+                __syncwarp();
+                cex_s[warp][lane] = __ldg(cex + lane);
+                cex_s[warp][32 + lane] = __ldg(cex + 32 + lane);
+                __syncwarp();
+            }
+            const int4 *cex4 = reinterpret_cast<const int4 *>(cex_s[warp]);
             if (MODE == 0) fresh = true;
             for (int s = 0; s < g.S && ok; ++s)
                 for (int t = 0; s + t < g.S && ok; ++t)
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             int ce[32];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
-                                const int4 v = __ldg(cex4 + 8 * q + i);
+                                const int4 v = cex4[8 * q + i];
                                 ce[4 * i] = v.x;
                                 ce[4 * i + 1] = v.y;
                                 ce[4 * i + 2] = v.z;

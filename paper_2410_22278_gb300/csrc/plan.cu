@@ -410,6 +410,15 @@ static int alloc_ws(Plan *P)
               al(&w.T2, n2) && al(&w.M, 2 * (size_t)gc * n2) && al(&w.Z, 2 * (size_t)gc * n2) && al(&w.rho, 2 * (size_t)gc) && al(&w.rho_part, 2 * (size_t)gc * kSlabSplitsMax) &&
               al(&w.dmax, (size_t)P->nshell * P->nshell) && al(&w.scal, 16) && (!mixed || al((double **)&w.Dpf, (n2 + 1) / 2)) &&
               (!mixed || al((double **)&w.dmaxf, ((size_t)P->nshell * P->nshell + 1) / 2));
+    {
+        // J-engine arrays: stride N_H(2 lmax)
+        int lmax = 0;
+        for (auto &sh : P->shells) lmax = std::max(lmax, sh.l);
+        const int L2 = 2 * lmax;
+        w.hs = (L2 + 1) * (L2 + 2) * (L2 + 3) / 6;
+        const size_t nh = std::max<size_t>(1, P->ppi.size()) * w.hs;
+        ok = ok && al(&w.DhD, nh) && al(&w.JH, nh) && al((double **)&w.DhF, (nh + 1) / 2);
+    }
     if (!ok) return fail(JK_ERR_OOM, "cudaMalloc failed for build workspace");
     // the structure-factor kernels write only the entries of shell pairs with
     // images, the same ones for every G; the others must read as zero
@@ -625,7 +634,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
                     x.K = cn[sF.p0 + pa] * cn[sS.p0 + pb] * std::exp(-a * b / p * AB2);
                     pv.push_back(x);
                     abv.push_back(make_double2(a, b));
-                    Q += std::pow(2.0, 0.25) * std::fabs(x.K) * std::pow(kPi / p, 1.25);  // Eq. 445 per primitive
+                    Q += std::pow(2.0, 0.25) * std::fabs(x.K) * std::pow(kPi / p, 1.25);  // Eq. pbc_eri_cauchy_schwarz_cutoff_definition per primitive
                 }
                 {
                     std::vector<int> ord(pv.size());
@@ -755,7 +764,7 @@ int build_plan(const jk_cell *cell, const jk_shell *shells, int nshell, double o
     }
     // ---- quartet counts (unique pairs of images): Schwarz-significant ones
     // by the exact factors (the quartets/s unit), and the FP64 share the
-    // mixed policy would take by the Eq. 445 estimates
+    // mixed policy would take by the Eq. pbc_eri_cauchy_schwarz_cutoff_definition estimates
     {
         long long N = (long long)P->spi.size();
         P->n_quartets = N * (N + 1) / 2;
@@ -1066,7 +1075,7 @@ void destroy_plan(Plan *P)
     release_cache(P);
     void *ptrs[] = {P->d_shells, P->d_spi, P->d_ppi, P->d_ppf, P->d_ppB, P->d_r1f, P->d_spair, P->d_spi_order, P->d_boys, P->d_boys_f, P->d_r1, P->d_gvec,
                     P->d_g0, P->d_compf, P->d_ppi_ab, P->d_kblk, P->d_kblk2, P->d_pvals, P->d_gtab0, P->d_ppi_pidx, P->d_phase, P->d_ppdf, P->d_gdf, P->d_phasef, P->ws.gtab, P->ws.gtab2, P->d_S, P->ws.Dp, P->ws.X, P->ws.Y, P->ws.JLR, P->ws.KLR, P->ws.T1, P->ws.T2,
-                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.rho_part, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
+                    P->ws.M, P->ws.Z, P->ws.rho, P->ws.rho_part, P->ws.DhD, P->ws.JH, P->ws.DhF, P->ws.dmax, P->ws.scal, P->ws.err, P->ws.cnt, P->ws.big, P->ws.nbig,
                     P->ws.Ms, P->ws.Zs, P->ws.Ds, P->ws.Mex, P->ws.Zex, P->ws.Dex, P->ws.Dpf, P->ws.dmaxf, P->ws.Cs, P->ws.Cex, P->ws.Kpart,
                     P->ws.lr.Vt, P->ws.lr.diag, P->ws.lr.done_row, P->ws.lr.sgn, P->ws.lr.rowmap, P->ws.lr.dyn, P->ws.lr.bar, P->ws.lr.Ct};
     for (void *p : ptrs)

@@ -45,6 +45,11 @@ struct Workspace {
     float *Dpf = nullptr;     // single-precision copies for the FP32 kernels (mixed precision)
     float *dmaxf = nullptr;
     double *scal = nullptr;   // small scalars (traces, energies)
+    // Coulomb-only builds (J-engine): per local primitive pair, hs Hermite
+    // density values (FP64 and FP32) and hs Hermite J accumulators
+    int hs = 0;
+    double *DhD = nullptr, *JH = nullptr;
+    float *DhF = nullptr;
     unsigned *err = nullptr;  // device check word
     unsigned long long *cnt = nullptr;  // kCounters build counters (see above)
     int2 *big = nullptr;                // compact list of quartets sent to FP64 (mixed precision)

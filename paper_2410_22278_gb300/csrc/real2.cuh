@@ -237,6 +237,7 @@ __device__ __forceinline__ void digest(const PlanDev &pl, const SpiRec &sb, cons
             for (int ab = 0; ab < NA * NB; ++ab) s += V[ab * NC * ND + c * ND + d] * Dij[ab];
             atomicAdd(X + (size_t)(aoK + c) * n + aoL + d, to_f64(T(2) * w * s));
         }
+    if (!Y) return;  // a Coulomb-only build
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real_q(PlanDev pl, int b0, int
                 atomicAdd(X + (size_t)(aoK + cd / ND) * n + aoL + cd % ND, to_f64(s2));
         }
         // exchange: the four index assignments of the orbit (the other four are transposes)
-        if (on) {
+        if (on && Y) {
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll

@@ -1,4 +1,5 @@
 // Real-space quartet kernels for bra class (0, 0) and ket class (1, 0) (generated by gen_units.py).
+#include "jeng.cuh"
 #include "launch.h"
 #include "real2.cuh"
 
@@ -46,6 +47,21 @@ void launch_real_q01(const RealLaunch &a)
         k_real_w<0, 0, 1, 0, double><<<grid, 32 * kWarpsPerBlock, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk,
                                                                                   a.mode, a.tau, a.Dp, a.dmax, a.X, a.Y, a.cnt, a.big,
                                                                                   a.nbig, a.cap, a.ovf);
+}
+
+void launch_jeng_q01(const RealLaunch &a)
+{
+    const int nb = a.b1 - a.b0, nk = a.k1 - a.k0;
+    if (nb <= 0 || nk <= 0) return;
+    dim3 grid((nb + kRealThreads - 1) / kRealThreads, (nk + a.kchunk - 1) / a.kchunk);
+    if (a.fp32)
+        k_jeng<0, 0, 1, 0, float><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                           a.tau, a.dmaxf, a.DhF, a.hs, a.X, a.JH, a.cnt, a.big, a.nbig,
+                                                                           a.cap, a.ovf);
+    else
+        k_jeng<0, 0, 1, 0, double><<<grid, kRealThreads, 0, a.st>>>(a.pl, a.b0, a.b1, a.k0, a.k1, a.same, a.kchunk, a.mode,
+                                                                            a.tau, a.dmax, a.DhD, a.hs, a.X, a.JH, a.cnt, a.big, a.nbig,
+                                                                            a.cap, a.ovf);
 }
 
 }  // namespace jk

@@ -247,3 +247,36 @@ def test_reciprocal_cache(jk, precision):
     J, K = build(plan, D2)
     assert np.abs(J - ref2[0]).max() < 1e-12
     plan.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coulomb_only_builds_match_oracle(jk, precision):
+    """A build that asks for J alone (K = NULL) skips the exchange and runs
+    the Hermite J-engine (Hermite ket densities, J in the Hermite basis, back
+    to Cartesian) for the class pairs with a d shell on both sides.  Its J
+    matches the oracle on s/p/d cells (the diamond-basis cell covers every
+    class pair up to (dd|dd)) and the J of a J+K build."""
+    cells = [sc.config(1), sc.small_random_cell(3, natom=2, lmax=2)]
+    refs = [oracle_jk(c)[:2] for c in cells]
+    if os.path.exists(GOLD_D1):
+        c1 = sc.diamond_cell(1)
+        cells.append(c1)
+        refs.append((O.density(c1), np.load(GOLD_D1)["J"]))
+    dev = torch.device("cuda:0")
+    for cell, (D, Jo) in zip(cells, refs):
+        plan = jk.plan_from_cell(cell, precision=precision)
+        Dt = torch.from_numpy(np.ascontiguousarray(D)).to(dev)
+        J1 = torch.full_like(Dt, float("nan"))
+        plan.build(Dt.data_ptr(), J1.data_ptr(), 0, 0)
+        J2 = torch.full_like(Dt, float("nan"))
+        K2 = torch.full_like(Dt, float("nan"))
+        plan.build(Dt.data_ptr(), J2.data_ptr(), K2.data_ptr(), 0)
+        torch.cuda.synchronize()
+        plan.close()
+        J1, J2 = J1.cpu().numpy(), J2.cpu().numpy()
+        tol = TOL64 * max(1.0, np.abs(Jo).max()) if precision == 0 else TOLMIX
+        print("%s precision %d J-engine: max|dJ| %.2e vs oracle, %.2e vs the J+K build"
+              % (cell.name, precision, np.abs(J1 - Jo).max(), np.abs(J1 - J2).max()))
+        assert np.abs(J1 - Jo).max() < tol
+        assert np.abs(J1 - J2).max() < tol
+        assert np.abs(J1 - J1.T).max() < 1e-12
