@@ -2,6 +2,13 @@
 
 Compiles every translation unit under csrc/ with nvcc in parallel, then
 links one shared library that exports the C ABI of include/jk.h.
+
+The real-space quartet units (csrc/real_q*.cu) are compiled with
+single-precision division and square root to within 2 ulp instead of
+correctly rounded, and with subnormal single-precision values flushed to
+zero.  Their FP32 kernels evaluate quartets whose error budget is set by the
+precision switch (relative errors of a few ulp of FP32 per term, far below
+it); the FP64 kernels of the same units are unaffected by these options.
 """
 from __future__ import annotations
 
@@ -20,6 +27,12 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
+FAST_F32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+
+
+def unit_flags(src):
+    """Per-unit nvcc options (the real-space quartet units: FAST_F32)."""
+    return FLAGS + (FAST_F32 if os.path.basename(src).startswith("real_q") else [])
 
 
 def sources():
@@ -34,13 +47,18 @@ def _headers_mtime():
 
 def _compile(src, verbose=False):
     obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
+    flags = unit_flags(src)
+    stamp = obj + ".flags"
+    same_flags = os.path.exists(stamp) and open(stamp).read() == " ".join(flags)
+    if same_flags and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj, ""
-    cmd = [NVCC] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [NVCC] + ARCH + flags + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
     os.replace(obj + ".tmp", obj)
+    with open(stamp, "w") as f:
+        f.write(" ".join(flags))
     return obj, r.stderr
 
 

@@ -264,7 +264,7 @@ static int reciprocal_phase(Plan *P, double *J, double *K, cudaStream_t st)
     // the D-independent structure factors (and their exchange slices) come
     // from the reciprocal cache once a build has filled it
     RecipCache &cache = P->cache;
-    const bool fill_cache = cache.on && !cache.valid;
+    const bool fill_cache = cache.on && !cache.m_valid;
     for (int g0 = 0, chunk = 0; g0 < ng; g0 += w.gc, ++chunk) {
         const int gcur = std::min(w.gc, ng - g0);
         double *Mc = cache.on ? cache.M + 2 * (size_t)g0 * n2 : w.M;
@@ -308,7 +308,10 @@ static int reciprocal_phase(Plan *P, double *J, double *K, cudaStream_t st)
         }
     }
     // filled in stream order: later builds on this plan are ordered after this one
-    if (fill_cache && (!mixed || K)) cache.valid = true;
+    if (cache.on) {
+        cache.m_valid = true;
+        if (mixed && K) cache.s_valid = true;
+    }
     if (mixed && K) {
         ev = tm.start(4);
         if ((rc = ozaki_finish(P, st))) return rc;

@@ -634,7 +634,7 @@ int ozaki_exchange_chunk(Plan *P, int chunk, const double *Mc, int m2, int S, cu
     const CUtensorMap &tmM = cached ? cc.tm_Ms : w.tm_Ms;
     const int mrow0 = cached ? (int)cc.row0[chunk] : 0;
     int ev = tm.start(8);
-    if (!cached || !cc.valid) slice(Mc, n, n, n, (long long)n * n, npad, npad, S, m2, Ms, Mex, st);
+    if (!cached || !cc.s_valid) slice(Mc, n, n, n, (long long)n * n, npad, npad, S, m2, Ms, Mex, st);
     tm.stop(8, ev, 1);
     {
         // dense form: Zt_b = (D M_b)^T, as (hi, lo) pairs ...
@@ -755,7 +755,6 @@ int cache_reciprocal(Plan *P, size_t max_bytes)
         return fail(JK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the reciprocal cache");
     }
     c.on = true;
-    c.valid = false;
     c.bytes = need;
     return JK_OK;
 }

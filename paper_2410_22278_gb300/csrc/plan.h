@@ -101,7 +101,9 @@ struct PhaseTimer {
 // exchange slices and row exponents.  Filled by the first build after it is
 // switched on; later builds skip the structure factors and their slicing.
 struct RecipCache {
-    bool on = false, valid = false;
+    // m_valid: the structure factors M are filled; s_valid: so are the
+    // exchange slices (mixed plans; a Coulomb-only build fills M alone)
+    bool on = false, m_valid = false, s_valid = false;
     size_t bytes = 0;
     double *M = nullptr;              // [2 * ng][n][n]
     __nv_bfloat16 *Ms = nullptr;      // chunk c at rows [row0[c], ...) of a (rows x npad) matrix

@@ -218,7 +218,8 @@ def test_every_kernel_family_matches_oracle(jk, family, precision):
 def test_reciprocal_cache(jk, precision):
     """jk_plan_cache: the build that fills the cache and the builds that read
     it give the uncached result (the cached data are D-independent), also
-    for a different density; 0 releases the cache."""
+    for a different density and after Coulomb-only builds; 0 releases the
+    cache."""
     cell = sc.small_random_cell(4, natom=3, lmax=1)
     dev = torch.device("cuda:0")
     D1 = torch.from_numpy(O.density(cell)).to(dev)
@@ -246,6 +247,17 @@ def test_reciprocal_cache(jk, precision):
     assert e.value.status == jk.JK_ERR_OOM
     J, K = build(plan, D2)
     assert np.abs(J - ref2[0]).max() < 1e-12
+    # a Coulomb-only build fills the structure factors alone; the next J+K
+    # build forms the exchange slices from them, and later ones reuse both
+    assert plan.cache(1 << 30) > 0
+    for D, ref, with_k in [(D1, ref1, False), (D2, ref2, False), (D2, ref2, True), (D1, ref1, True)]:
+        J = torch.empty_like(D)
+        K = torch.empty_like(D) if with_k else None
+        plan.build(D.data_ptr(), J.data_ptr(), K.data_ptr() if with_k else 0, 0)
+        torch.cuda.synchronize()
+        assert np.abs(J.cpu().numpy() - ref[0]).max() < 1e-12
+        if with_k:
+            assert np.abs(K.cpu().numpy() - ref[1]).max() < 1e-12
     plan.close()
 
 
