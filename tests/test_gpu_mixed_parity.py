@@ -188,15 +188,17 @@ def test_two_threads_one_plan(jk):
 
 
 @pytest.mark.parametrize("family", [0, 1, 2])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, "fp32"])
 def test_every_kernel_family_matches_oracle(jk, family, precision):
     """The s and p class pairs have three real-space kernel families (lane
     per bra, warp per bra, pair queue); each, forced through
     jk_plan_set_schedule for every such class pair, matches the oracle on a
-    skewed s/p/d cell."""
+    skewed s/p/d cell, in FP64, in the mixed form and with every quartet
+    forced to FP32 (the FP32 rounding bound)."""
     cell = sc.small_random_cell(3, natom=2, lmax=2)
     D, Jo, Ko, _ = oracle_jk(cell)
-    plan = jk.plan_from_cell(cell, precision=precision)
+    forced = precision == "fp32"
+    plan = jk.plan_from_cell(cell, precision=jk.JK_MIXED if forced else precision, mixed_switch=1e30 if forced else 0.0)
     classes = [(a, b) for a in range(6) for b in range(a, 6)]
     plan.set_schedule([(family if (a <= 2 and b <= 2) else 0, 512 if (family == 1 and a <= 2 and b <= 2) else 16)
                        for a, b in classes])
@@ -206,7 +208,13 @@ def test_every_kernel_family_matches_oracle(jk, family, precision):
     K = torch.empty_like(Dt)
     plan.build(Dt.data_ptr(), J.data_ptr(), K.data_ptr(), 0)
     torch.cuda.synchronize()
+    n64, n32 = plan.build_counts()[:2]
     plan.close()
+    if forced:
+        assert n32 > 0.9 * (n32 + n64), (n32, n64)
+        assert np.abs(J.cpu().numpy() - Jo).max() < TOL_FP32_REL * max(1.0, np.abs(Jo).max())
+        assert np.abs(K.cpu().numpy() - Ko).max() < TOL_FP32_REL * max(1.0, np.abs(Ko).max())
+        return
     tol = (TOL64 * max(1.0, np.abs(Jo).max())) if precision == 0 else TOLMIX
     assert np.abs(J.cpu().numpy() - Jo).max() < tol
     assert np.abs(K.cpu().numpy() - Ko).max() < tol
