@@ -132,10 +132,14 @@ int jk_pair_counts(const jk_cell *cell, const jk_shell *shells, int nshell, doub
 /* Keep the plan's D-independent reciprocal-space data resident between
  * builds (no counterpart in the paper, which recomputes its reciprocal
  * terms per quartet): the pair structure factors of every reciprocal vector
- * (2 n_G nbf^2 FP64) and, for JK_MIXED plans, their BF16 exchange slices.
- * The next jk_build fills the cache; later builds skip the structure
- * factors and their slicing, which for an SCF loop or repeated frames of
- * one geometry are the same every build.  Allocated at once if the total
+ * (2 n_G nbf^2 FP64 for JK_FP64 plans; for JK_MIXED plans their upper
+ * triangles, 2 n_G nbf (nbf + 1) / 2 FP64, which is all the Coulomb
+ * contraction needs since they are symmetric in the two basis indices, and
+ * their BF16 exchange slices).  The next jk_build fills the cache (a
+ * Coulomb-only build fills the structure factors; the first build with K
+ * adds the slices); later builds skip the structure factors and their
+ * slicing, which for an SCF loop or repeated frames of one geometry are the
+ * same every build.  Allocated at once if the total
  * fits max_bytes, else JK_ERR_OOM (the plan then works as before);
  * max_bytes = 0 releases it.  *bytes (may be NULL) receives the size.
  * Waits for the plan's last build.  jk_plan_info's device_bytes includes

@@ -81,6 +81,45 @@ __global__ void k_dot2(size_t n2, const double *__restrict__ B, const double *__
     }
 }
 
+// Packed upper triangles (row-major, i <= j): entry (i, j) at
+// i n - i (i - 1) / 2 + j - i.  The structure factors M_b are symmetric in
+// their two basis indices (each unique shell pair writes both blocks), so
+// the Coulomb contraction needs one triangle: rho_b = sum_{i<=j} M_b(ij)
+// Ds(ij) with Ds the symmetrised density (D'_ij + D'_ji off the diagonal),
+// and J_LR(ij) = J_LR(ji) = sum_b M_b(ij) rho_b.
+__device__ __forceinline__ long long tri_index(long long n, long long i, long long j) { return i * n - i * (i - 1) / 2 + j - i; }
+
+// Ap[b] = upper triangle of A[b] for nb matrices n x n
+__global__ void k_pack_upper(int n, long long npk, int nb, const double *__restrict__ A, double *__restrict__ Ap)
+{
+    const long long n2 = (long long)n * n, tot = n2 * nb;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (long long)gridDim.x * blockDim.x) {
+        const long long b = idx / n2, r = idx - b * n2, i = r / n, j = r - i * n;
+        if (j >= i) Ap[b * npk + tri_index(n, i, j)] = A[idx];
+    }
+}
+
+// Ds = packed D + D^T off the diagonal, D on it
+__global__ void k_sym_density(int n, const double *__restrict__ D, double *__restrict__ Ds)
+{
+    const long long n2 = (long long)n * n;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n2; idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / n, j = idx - i * n;
+        if (j > i) Ds[tri_index(n, i, j)] = D[idx] + D[j * n + i];
+        else if (j == i) Ds[tri_index(n, i, i)] = D[idx];
+    }
+}
+
+// J (n x n) = the symmetric matrix of the packed Jp
+__global__ void k_unpack_sym(int n, const double *__restrict__ Jp, double *__restrict__ J)
+{
+    const long long n2 = (long long)n * n;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n2; idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / n, j = idx - i * n;
+        J[idx] = Jp[i <= j ? tri_index(n, i, j) : tri_index(n, j, i)];
+    }
+}
+
 // J = F o (X + X^T + JLR + c tr S), K = F o (Y + Y^T + KLR + c SDS)
 __global__ void k_final(int n, const double *__restrict__ f, const double *__restrict__ X, const double *__restrict__ Y,
                         const double *__restrict__ JLR, const double *__restrict__ KLR, const double *__restrict__ S,
@@ -262,13 +301,32 @@ static int reciprocal_phase(Plan *P, double *J, double *K, cudaStream_t st)
     // mixed precision: structure factors in double-float on the FP32 pipe
     const bool sfac_df = mixed && P->sfac_df && w.gtab2;
     // the D-independent structure factors (and their exchange slices) come
-    // from the reciprocal cache once a build has filled it
+    // from the reciprocal cache once a build has filled it; a mixed plan
+    // caches them as packed upper triangles for the Coulomb contraction (the
+    // exchange reads its BF16 slices), an FP64 plan in full
     RecipCache &cache = P->cache;
-    const bool fill_cache = cache.on && !cache.m_valid;
+    const bool packed = cache.on && mixed;
+    const long long npk = (long long)n * (n + 1) / 2;
+    if (J && packed) {
+        // symmetrised density and the packed J_LR accumulator in the
+        // epilogue's scratch (free until the epilogue)
+        k_sym_density<<<grid_for(n2), 256, 0, st>>>(n, w.Dp, w.T1);
+        cudaMemsetAsync(w.T2, 0, npk * sizeof(double), st);
+    }
     for (int g0 = 0, chunk = 0; g0 < ng; g0 += w.gc, ++chunk) {
         const int gcur = std::min(w.gc, ng - g0);
-        double *Mc = cache.on ? cache.M + 2 * (size_t)g0 * n2 : w.M;
-        if (!cache.on || fill_cache) {
+        // Mf: full structure factors of the chunk (formed here when needed);
+        // Mc: what the Coulomb contraction reads
+        double *Mf = w.M, *Mc = w.M;
+        bool form = true;
+        if (cache.on && !mixed) {
+            Mf = Mc = cache.M + 2 * (size_t)g0 * n2;
+            form = !cache.m_valid;
+        } else if (packed) {
+            Mc = cache.M + 2 * (size_t)g0 * npk;
+            form = !cache.m_valid || (K && !cache.s_valid);  // the exchange slices are cut from the full form
+        }
+        if (form) {
             ev = tm.start(2);
             int nsf = 0;
             const long long ne = (long long)P->pvals.size() * gcur;
@@ -276,10 +334,14 @@ static int reciprocal_phase(Plan *P, double *J, double *K, cudaStream_t st)
                                                                          sfac_df ? w.gtab2 : nullptr);
             for (int c = 0; c < JK_NCLASS_MAX; ++c) {
                 if (sfac_df)
-                    launch_sfac_df(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], g0, gcur, w.gtab2, Mc, st);
+                    launch_sfac_df(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], g0, gcur, w.gtab2, Mf, st);
                 else
-                    launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, Mc, st);
+                    launch_sfac(c, pl, P->spair_class_off[c], P->spair_class_off[c + 1], P->d_gvec, g0, gcur, w.gtab, Mf, st);
                 nsf += P->spair_class_off[c + 1] > P->spair_class_off[c];
+            }
+            if (packed && !cache.m_valid) {
+                k_pack_upper<<<152 * 16, 256, 0, st>>>(n, npk, 2 * gcur, Mf, Mc);
+                ++nsf;
             }
             if ((rc = cuda_check("structure factors"))) return rc;
             tm.stop(2, ev, nsf + 1);
@@ -288,26 +350,32 @@ static int reciprocal_phase(Plan *P, double *J, double *K, cudaStream_t st)
         if (J) {
             // rho_D = M^T vec(D'), J_LR += M rho_D (two passes over the slab)
             ev = tm.start(3);
-            slab_gemv_t(Mc, (long long)n2, m2, w.Dp, w.rho_part, w.rho, st);
-            slab_gemv_n(Mc, (long long)n2, m2, w.rho, 1.0, w.JLR, st);
+            if (packed) {
+                slab_gemv_t(Mc, npk, m2, w.T1, w.rho_part, w.rho, st);
+                slab_gemv_n(Mc, npk, m2, w.rho, 1.0, w.T2, st);
+            } else {
+                slab_gemv_t(Mc, (long long)n2, m2, w.Dp, w.rho_part, w.rho, st);
+                slab_gemv_n(Mc, (long long)n2, m2, w.rho, 1.0, w.JLR, st);
+            }
             tm.stop(3, ev, 3);
         }
         if (K) {
             ev = tm.start(4);
             if (mixed) {
                 // split-precision BF16 tensor-core GEMMs, slices per chunk from its G bound
-                if ((rc = ozaki_exchange_chunk(P, chunk, Mc, m2, w.chunk_slices[chunk], st))) return rc;
+                if ((rc = ozaki_exchange_chunk(P, chunk, Mf, m2, w.chunk_slices[chunk], st))) return rc;
                 tm.stop(4, ev, 4);
             } else {
                 // the plain FP64 form: Z_b = D' M_b, then K_LR += sum_b M_b Z_b
                 // (upper tiles; the product is symmetric), FP64 GEMMs
-                dgemm_batched(n, n, n, w.Dp, n, 0, Mc, n, (long long)n2, w.Z, n, (long long)n2, m2, 1.0, 0.0, false, st);
-                dgemm_batched(n, n, n, Mc, n, (long long)n2, w.Z, n, (long long)n2, w.KLR, n, 0, m2, 1.0, 0.0, true, st);
+                dgemm_batched(n, n, n, w.Dp, n, 0, Mf, n, (long long)n2, w.Z, n, (long long)n2, m2, 1.0, 0.0, false, st);
+                dgemm_batched(n, n, n, Mf, n, (long long)n2, w.Z, n, (long long)n2, w.KLR, n, 0, m2, 1.0, 0.0, true, st);
                 tm.stop(4, ev, 2);
             }
         }
     }
     // filled in stream order: later builds on this plan are ordered after this one
+    if (J && packed) k_unpack_sym<<<grid_for(n2), 256, 0, st>>>(n, w.T2, w.JLR);
     if (cache.on) {
         cache.m_valid = true;
         if (mixed && K) cache.s_valid = true;

@@ -716,7 +716,9 @@ int cache_reciprocal(Plan *P, size_t max_bytes)
     const int ng = (int)(P->gvec.size() / 4);
     const size_t n2 = (size_t)P->nbf * P->nbf;
     RecipCache &c = P->cache;
-    size_t bM = 2 * (size_t)ng * n2 * sizeof(double), bS = 0, bX = 0;
+    // mixed plans keep the structure factors as packed upper triangles
+    const size_t npk = (size_t)P->nbf * (P->nbf + 1) / 2;
+    size_t bM = 2 * (size_t)ng * (P->precision == JK_MIXED ? npk : n2) * sizeof(double), bS = 0, bX = 0;
     long long rows = 0, ex = 0;
     const bool mixed = P->precision == JK_MIXED;
     if (mixed) {

@@ -105,7 +105,7 @@ struct RecipCache {
     // exchange slices (mixed plans; a Coulomb-only build fills M alone)
     bool on = false, m_valid = false, s_valid = false;
     size_t bytes = 0;
-    double *M = nullptr;              // [2 * ng][n][n]
+    double *M = nullptr;              // [2 * ng][n][n] (FP64 plans) or [2 * ng][n (n + 1) / 2] packed upper triangles (mixed)
     __nv_bfloat16 *Ms = nullptr;      // chunk c at rows [row0[c], ...) of a (rows x npad) matrix
     int *Mex = nullptr;               // chunk c at ex0[c]
     std::vector<long long> row0, ex0;
