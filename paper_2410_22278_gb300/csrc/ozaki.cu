@@ -84,23 +84,27 @@ __global__ void k_ozaki_slice(const double *__restrict__ X, int rows, int cols, 
     if (lane == 0) ex[(size_t)b * rows_pad + r] = sigma;
     __nv_bfloat16 *o = out + ((size_t)b * S * rows_pad + r) * cols_pad;
     const size_t sstride = (size_t)rows_pad * cols_pad;
-    for (int k = lane; k < cols_pad; k += 32) {
-        long long V = 0;
-        if (r < rows && k < cols) {
-            const unsigned long long bits = row[k];
-            const int E = (int)((bits >> 52) & 0x7ff);
-            if (E > 0) {  // subnormals flush to zero
-                const unsigned long long M = (bits & 0xfffffffffffffull) | (1ull << 52);
-                const int sh = E - 1013 - sigma;  // <= 9, so F < 2^62
-                const unsigned long long F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
-                V = (bits >> 63) ? -(long long)F : (long long)F;
-            }
-        }
+    auto scaled = [&](int k) -> long long {
+        if (r >= rows || k >= cols) return 0;
+        const unsigned long long bits = row[k];
+        const int E = (int)((bits >> 52) & 0x7ff);
+        if (E == 0) return 0;  // zero; subnormals flush to zero
+        const unsigned long long M = (bits & 0xfffffffffffffull) | (1ull << 52);
+        const int sh = E - 1013 - sigma;  // <= 9, so F < 2^62
+        const unsigned long long F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
+        return (bits >> 63) ? -(long long)F : (long long)F;
+    };
+    // two adjacent columns per lane, stored as one bf16 pair per slice
+    // (cols_pad and the slice stride are even)
+    for (int k = 2 * lane; k < cols_pad; k += 64) {
+        long long V0 = scaled(k), V1 = scaled(k + 1);
         for (int s = 0; s < S; ++s) {
             const int shift = 55 - 8 * s;
-            const long long d = (V + (1LL << (shift - 1))) >> shift;  // arithmetic shift: floor
-            V -= d * (1LL << shift);
-            o[s * sstride + k] = __float2bfloat16_rn((float)d);
+            const long long d0 = (V0 + (1LL << (shift - 1))) >> shift;  // arithmetic shift: floor
+            const long long d1 = (V1 + (1LL << (shift - 1))) >> shift;
+            V0 -= d0 * (1LL << shift);
+            V1 -= d1 * (1LL << shift);
+            *reinterpret_cast<__nv_bfloat162 *>(o + s * sstride + k) = __floats2bfloat162_rn((float)d0, (float)d1);
         }
     }
 }
@@ -480,17 +484,30 @@ __global__ void k_ozaki_slice_pair(const float2 *__restrict__ X, int rows, int c
         const unsigned long long F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
         return (u >> 31) ? -(long long)F : (long long)F;
     };
-    for (int k = lane; k < cols_pad; k += 32) {
-        long long V = 0;
-        if (r < rows && k < cols) {
-            const float2 x = row[k];
-            V = part(x.x) + part(x.y);
+    // the low-rank Y is read by the GEMMs up to its live columns (a multiple
+    // of 128); the dense form through cols_pad
+    const int cend = dyn_mode == 2 ? min(cols_pad, (cols + 127) / 128 * 128) : cols_pad;
+    // two adjacent columns per lane, stored as one bf16 pair per slice
+    // (cols_pad and the slice stride are even)
+    for (int k = 2 * lane; k < cend; k += 64) {
+        long long V0 = 0, V1 = 0;
+        if (r < rows) {
+            if (k < cols) {
+                const float2 x = row[k];
+                V0 = part(x.x) + part(x.y);
+            }
+            if (k + 1 < cols) {
+                const float2 x = row[k + 1];
+                V1 = part(x.x) + part(x.y);
+            }
         }
         for (int s = 0; s < S; ++s) {
             const int shift = 55 - 8 * s;
-            const long long d = (V + (1LL << (shift - 1))) >> shift;  // arithmetic shift: floor
-            V -= d * (1LL << shift);
-            o[s * sstride + k] = __float2bfloat16_rn((float)d);
+            const long long d0 = (V0 + (1LL << (shift - 1))) >> shift;  // arithmetic shift: floor
+            const long long d1 = (V1 + (1LL << (shift - 1))) >> shift;
+            V0 -= d0 * (1LL << shift);
+            V1 -= d1 * (1LL << shift);
+            *reinterpret_cast<__nv_bfloat162 *>(o + s * sstride + k) = __floats2bfloat162_rn((float)d0, (float)d1);
         }
     }
 }
