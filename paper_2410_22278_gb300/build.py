@@ -3,12 +3,9 @@
 Compiles every translation unit under csrc/ with nvcc in parallel, then
 links one shared library that exports the C ABI of include/jk.h.
 
-The real-space quartet units (csrc/real_q*.cu) are compiled with
-single-precision division and square root to within 2 ulp instead of
-correctly rounded, and with subnormal single-precision values flushed to
-zero.  Their FP32 kernels evaluate quartets whose error budget is set by the
-precision switch (relative errors of a few ulp of FP32 per term, far below
-it); the FP64 kernels of the same units are unaffected by these options.
+The real-space quartet units (csrc/real_q*.cu) are compiled with subnormal
+single-precision values flushed to zero (terms below 1.2e-38 are far under
+anything digested); the FP64 kernels of the same units are unaffected.
 """
 from __future__ import annotations
 
@@ -27,7 +24,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
-FAST_F32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+FAST_F32 = ["-ftz=true"]
 
 
 def unit_flags(src):

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kRealThreads) k_jeng(PlanDev pl, int b0, int b
         if (sizeof(T) == 4 && valid && mode) {
             const float dm = quartet_dmax(reinterpret_cast<const float *>(dmax), nsh, sb, sk);
             const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
-            const float ipq = 1.0f / sb.pmin + 1.0f / sk.pmin;
+            const float ipq = frcp_fast(sb.pmin) + frcp_fast(sk.pmin);
             if (est >= tauf || ipq > 0.7225f * (ipq + pl.inv_omega2f)) {
                 const unsigned slot = atomicAdd(nbig, 1u);
                 if (slot < cap) {
@@ -209,17 +209,17 @@ __global__ void __launch_bounds__(kRealThreads) k_jeng(PlanDev pl, int b0, int b
                     const PpiF xf = pl.ppf[bp];
                     // screening radius (single precision), as in quartet_block
                     const float ipf = xf.pad, iqf = yf.pad;
-                    const float awf = 1.0f / (ipf + iqf + pl.inv_omega2f);
-                    const float cwf = sqrtf(awf * (ipf + iqf));
+                    const float awf = frcp_fast(ipf + iqf + pl.inv_omega2f);
+                    const float cwf = fsqrt_fast(awf * (ipf + iqf));
                     const float preff = 34.986836655249725f * xf.K * yf.K * ipf * iqf * rsqrtf(xf.p + yf.p);
                     ++tl.screen;
                     const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
                     if (!(lg > 0.0f)) continue;
                     ++tl.radius;
-                    float r = sqrtf(lg / awf);
+                    float r = fsqrt_fast(fdiv_fast(lg, awf));
                     if (L > 0) {
-                        r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
-                        r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+                        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
+                        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
                         r += 0.5f + 0.25f * L;
                     }
                     const float r2 = r * r;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kRealThreads) k_jeng(PlanDev pl, int b0, int b
                             X0[a] -= f[0] * latc(pl.L, pl.Lf, a, T(0)) + f[1] * latc(pl.L, pl.Lf, 3 + a, T(0)) +
                                      f[2] * latc(pl.L, pl.Lf, 6 + a, T(0));
                     }
-                    const float x0n = sqrtf((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
+                    const float x0n = fsqrt_fast((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
                     T Rs[D * D * D];
 #pragma unroll
                     for (int q = 0; q < D * D * D; ++q) Rs[q] = T(0);

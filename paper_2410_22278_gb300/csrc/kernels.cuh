@@ -187,18 +187,18 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
             const PpiF yf = pl.ppf[sk.pp0 + j];
             // ---- screening, single precision
             const float ipf = xf.pad, iqf = yf.pad;
-            const float awf = 1.0f / (ipf + iqf + iw2);
-            const float cwf = sqrtf(awf * (ipf + iqf));
+            const float awf = frcp_fast(ipf + iqf + iw2);
+            const float cwf = fsqrt_fast(awf * (ipf + iqf));
             const float preff = 34.986836655249725f * xf.K * yf.K * ipf * iqf * rsqrtf(xf.p + yf.p);
             ++tl.screen;
 
             const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
             if (!(lg > 0.0f)) continue;
             ++tl.radius;
-            float r = sqrtf(lg / awf);
+            float r = fsqrt_fast(fdiv_fast(lg, awf));
             if (L > 0) {
-                r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
-                r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+                r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
+                r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
                 // the Gaussian bound is derived for s functions; widen for L > 0
                 r += 0.5f + 0.25f * L;
             }
@@ -217,7 +217,7 @@ __device__ __forceinline__ void quartet_block(const PlanDev &pl, const SpiRec &s
                 for (int a = 0; a < 3; ++a)
                     X0[a] -= f[0] * latc(pl.L, pl.Lf, a, T(0)) + f[1] * latc(pl.L, pl.Lf, 3 + a, T(0)) + f[2] * latc(pl.L, pl.Lf, 6 + a, T(0));
             }
-            const float x0n = sqrtf((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
+            const float x0n = fsqrt_fast((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
             T Rs[D * D * D];
 #pragma unroll
             for (int k = 0; k < D * D * D; ++k) Rs[k] = T(0);
@@ -325,11 +325,11 @@ __device__ __forceinline__ bool reaches(const PlanDev &pl, const SpiRec &sb, flo
     const float B0 = 24.7394241f * sb.S * kS * 1.001f;  // 2 pi^{5/2} / sqrt 2
     const float lg = __logf(B0) - pl.log_ewald_R;
     if (!(lg > 0.0f)) return false;
-    const float aw = 1.0f / (1.0f / sb.pmin + 1.0f / kpmin + pl.inv_omega2f);
-    float r = sqrtf(lg / aw);
+    const float aw = frcp_fast(frcp_fast(sb.pmin) + frcp_fast(kpmin) + pl.inv_omega2f);
+    float r = fsqrt_fast(fdiv_fast(lg, aw));
     if (L > 0) {
-        r = sqrtf((lg + L * __logf(1.0f + 2.0f * aw * r)) / aw);
-        r = sqrtf((lg + L * __logf(1.0f + 2.0f * aw * r)) / aw);
+        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * aw * r), aw));
+        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * aw * r), aw));
     }
     r = r * 1.0001f + (L > 0 ? 0.5f + 0.25f * L : 0.0f) + sb.ext + kext + 1e-3f;
     const float X[3] = {sb.Pc[0] - kx, sb.Pc[1] - ky, sb.Pc[2] - kz};
@@ -382,15 +382,15 @@ __device__ __forceinline__ float quartet_estimate(const PlanDev &pl, const SpiRe
     for (int a = 0; a < 3; ++a) f[a] = rintf(pl.Finvf[3 * a] * X[0] + pl.Finvf[3 * a + 1] * X[1] + pl.Finvf[3 * a + 2] * X[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) X[a] -= f[0] * pl.Lf[a] + f[1] * pl.Lf[3 + a] + f[2] * pl.Lf[6 + a];
-    const float d = fmaxf(0.0f, sqrtf(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
+    const float d = fmaxf(0.0f, fsqrt_fast(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
     const float d2 = d * d, iw2 = pl.inv_omega2f;
     float est = 0.0f;
     for (int i = 0; i < sb.npp; ++i) {
         const PpiF x = pl.ppf[sb.pp0 + i];
         for (int j = 0; j < sk.npp; ++j) {
             const PpiF y = pl.ppf[sk.pp0 + j];
-            const float aw = 1.0f / (x.pad + y.pad + iw2);
-            const float cw = sqrtf(aw * (x.pad + y.pad));
+            const float aw = frcp_fast(x.pad + y.pad + iw2);
+            const float cw = fsqrt_fast(aw * (x.pad + y.pad));
             est += 34.986836655249725f * fabsf(x.K * y.K) * x.pad * y.pad * rsqrtf(x.p + y.p) * (1.0f - cw) * __expf(-aw * d2);
         }
     }
@@ -416,8 +416,8 @@ __device__ __forceinline__ float quartet_estimate_bound(const PlanDev &pl, const
     for (int a = 0; a < 3; ++a) f[a] = rintf(pl.Finvf[3 * a] * X[0] + pl.Finvf[3 * a + 1] * X[1] + pl.Finvf[3 * a + 2] * X[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) X[a] -= f[0] * pl.Lf[a] + f[1] * pl.Lf[3 + a] + f[2] * pl.Lf[6 + a];
-    const float d = fmaxf(0.0f, sqrtf(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
-    const float aw = 1.0f / (1.0f / sb.pmin + 1.0f / sk.pmin + pl.inv_omega2f);
+    const float d = fmaxf(0.0f, fsqrt_fast(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) - sb.ext - sk.ext);
+    const float aw = frcp_fast(frcp_fast(sb.pmin) + frcp_fast(sk.pmin) + pl.inv_omega2f);
     return 24.7394241f * 1.001f * sb.S * sk.S * __expf(-aw * d * d);
 }
 
@@ -427,8 +427,14 @@ __device__ __forceinline__ float quartet_estimate_bound(const PlanDev &pl, const
 // FP64 by k_real_list) instead of being evaluated here; if the list is full
 // the quartet is evaluated here and counted in ovf.  *cnt counts the image
 // quartets this launch evaluated.
+// Resident blocks per SM asked of the compiler for the lane-per-bra kernel:
+// four for the classes of total momentum up to 2 (up to 128 registers, so
+// that their blocks stay in registers; left to itself the compiler takes 64
+// for (ss|ss) and spills), the compiler's choice for the others.
+constexpr int real_min_blocks(int L) { return L <= 2 ? 4 : 1; }
+
 template <int LA, int LB, int LC, int LD, typename T>
-__global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
+__global__ void __launch_bounds__(kRealThreads, real_min_blocks(LA + LB + LC + LD)) k_real(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
                                                         double tau, const T *__restrict__ Dp, const T *__restrict__ dmax,
                                                         double *__restrict__ X, double *__restrict__ Y,
                                                         unsigned long long *__restrict__ cnt, int2 *__restrict__ big,
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b
             const float dm = quartet_dmax(reinterpret_cast<const float *>(dmax), nsh, sb, sk);
             const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
             // largest c_w^2 = (1/p + 1/q) / (1/p + 1/q + 1/w^2) over the quartet's primitives
-            const float ipq = 1.0f / sb.pmin + 1.0f / sk.pmin;
+            const float ipq = frcp_fast(sb.pmin) + frcp_fast(sk.pmin);
             if (est >= tauf || ipq > 0.7225f * (ipq + pl.inv_omega2f)) {
                 const unsigned slot = atomicAdd(nbig, 1u);
                 if (slot < cap) {

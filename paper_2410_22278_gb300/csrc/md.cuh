@@ -190,6 +190,19 @@ __device__ __forceinline__ float boys_top(float T, const float *__restrict__ tab
     return fmaf(f, d, __ldg(row + 0));
 }
 
+// Screening arithmetic in single precision (it decides which terms to form,
+// not their values): approximate reciprocal, quotient and square root (within
+// 2 ulp; the radii carry margins far wider).  The terms themselves use the
+// correctly rounded operations.
+__device__ __forceinline__ float frcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fsqrt_fast(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ double erfc_(double x) { return erfc(x); }
 __device__ __forceinline__ float erfc_(float x) { return erfcf(x); }
 __device__ __forceinline__ double exp_(double x) { return exp(x); }

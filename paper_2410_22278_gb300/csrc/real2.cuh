@@ -57,15 +57,15 @@ template <int L>
 __device__ __forceinline__ bool prim_reaches(const PlanDev &pl, const PpiF &bf, const PpiF &kf)
 {
     const float ipf = bf.pad, iqf = kf.pad;
-    const float awf = 1.0f / (ipf + iqf + pl.inv_omega2f);
-    const float cwf = sqrtf(awf * (ipf + iqf));
+    const float awf = frcp_fast(ipf + iqf + pl.inv_omega2f);
+    const float cwf = fsqrt_fast(awf * (ipf + iqf));
     const float preff = 34.986836655249725f * bf.K * kf.K * ipf * iqf * rsqrtf(bf.p + kf.p);
     const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
     if (!(lg > 0.0f)) return false;
-    float r = sqrtf(lg / awf);
+    float r = fsqrt_fast(fdiv_fast(lg, awf));
     if (L > 0) {
-        r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
-        r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
+        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
         r += 0.5f + 0.25f * L;
     }
     float X0[3] = {bf.P[0] - kf.P[0], bf.P[1] - kf.P[1], bf.P[2] - kf.P[2]};
@@ -77,7 +77,7 @@ __device__ __forceinline__ bool prim_reaches(const PlanDev &pl, const PpiF &bf, 
     const float x2 = X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2];
     const float r2 = r * r;
     if (x2 < r2) return true;
-    const float x0n = sqrtf(x2);
+    const float x0n = fsqrt_fast(x2);
     for (int c = 1; c < pl.nr1; ++c) {
         if (pl.r1f[4 * c + 3] - x0n >= r) return false;
         const float Xx = X0[0] - pl.r1f[4 * c], Xy = X0[1] - pl.r1f[4 * c + 1], Xz = X0[2] - pl.r1f[4 * c + 2];
@@ -100,16 +100,16 @@ __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB,
     constexpr int NTA = LAB + 1, NTC = LCD + 1, D = L + 1;
     const float iw2 = pl.inv_omega2f;
     const float ipf = bf.pad, iqf = kf.pad;
-    const float awf = 1.0f / (ipf + iqf + iw2);
-    const float cwf = sqrtf(awf * (ipf + iqf));
+    const float awf = frcp_fast(ipf + iqf + iw2);
+    const float cwf = fsqrt_fast(awf * (ipf + iqf));
     const float preff = 34.986836655249725f * bf.K * kf.K * ipf * iqf * rsqrtf(bf.p + kf.p);
     ++tl.screen;
     const float lg = __logf(fabsf(preff) * (1.0f - cwf)) - pl.log_ewald_R;
     if (!(lg > 0.0f)) return;
-    float r = sqrtf(lg / awf);
+    float r = fsqrt_fast(fdiv_fast(lg, awf));
     if (L > 0) {
-        r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
-        r = sqrtf((lg + L * __logf(1.0f + 2.0f * awf * r)) / awf);
+        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
+        r = fsqrt_fast(fdiv_fast(lg + L * __logf(1.0f + 2.0f * awf * r), awf));
         r += 0.5f + 0.25f * L;  // the Gaussian bound is derived for s functions; widen for L > 0
     }
     const float r2 = r * r;
@@ -126,7 +126,7 @@ __device__ __forceinline__ void prim_term(const PlanDev &pl, const PrimE<LA, LB,
             X0[a] -= f[0] * latc(pl.L, pl.Lf, a, T(0)) + f[1] * latc(pl.L, pl.Lf, 3 + a, T(0)) + f[2] * latc(pl.L, pl.Lf, 6 + a, T(0));
     }
     ++tl.radius;
-    const float x0n = sqrtf((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
+    const float x0n = fsqrt_fast((float)(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2]));
     T Rs[D * D * D];
 #pragma unroll
     for (int q = 0; q < D * D * D; ++q) Rs[q] = T(0);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_real_w(PlanDev pl, int 
             // precision policy: large quartets (and short [c_w, 1] intervals) go to the FP64 list
             const float dm = quartet_dmax(reinterpret_cast<const float *>(dmax), nsh, sb, sk);
             const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
-            const float ipq = 1.0f / sb.pmin + 1.0f / sk.pmin;
+            const float ipq = frcp_fast(sb.pmin) + frcp_fast(sk.pmin);
             if (est >= tauf || ipq > 0.7225f * (ipq + pl.inv_omega2f)) {
                 const unsigned slot = atomicAdd(nbig, 1u);
                 if (slot < cap) {
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real_q(PlanDev pl, int b0, int
         if (sizeof(T) == 4 && valid && mode) {
             const float dm = quartet_dmax(reinterpret_cast<const float *>(dmax), nsh, sb, sk);
             const float est = quartet_estimate_bound(pl, sb, sk) * dm >= tauf ? quartet_estimate(pl, sb, sk) * dm : 0.0f;
-            const float ipq = 1.0f / sb.pmin + 1.0f / sk.pmin;
+            const float ipq = frcp_fast(sb.pmin) + frcp_fast(sk.pmin);
             if (est >= tauf || ipq > 0.7225f * (ipq + pl.inv_omega2f)) {
                 const unsigned slot = atomicAdd(nbig, 1u);
                 if (slot < cap) {
