@@ -427,14 +427,8 @@ __device__ __forceinline__ float quartet_estimate_bound(const PlanDev &pl, const
 // FP64 by k_real_list) instead of being evaluated here; if the list is full
 // the quartet is evaluated here and counted in ovf.  *cnt counts the image
 // quartets this launch evaluated.
-// Resident blocks per SM asked of the compiler for the lane-per-bra kernel:
-// four for the classes of total momentum up to 2 (up to 128 registers, so
-// that their blocks stay in registers; left to itself the compiler takes 64
-// for (ss|ss) and spills), the compiler's choice for the others.
-constexpr int real_min_blocks(int L) { return L <= 2 ? 4 : 1; }
-
 template <int LA, int LB, int LC, int LD, typename T>
-__global__ void __launch_bounds__(kRealThreads, real_min_blocks(LA + LB + LC + LD)) k_real(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
+__global__ void __launch_bounds__(kRealThreads) k_real(PlanDev pl, int b0, int b1, int k0, int k1, int same, int kchunk, int mode,
                                                         double tau, const T *__restrict__ Dp, const T *__restrict__ dmax,
                                                         double *__restrict__ X, double *__restrict__ Y,
                                                         unsigned long long *__restrict__ cnt, int2 *__restrict__ big,
